@@ -1,0 +1,363 @@
+"""Benchmark: batched HNSW search QPS at recall@10 >= 0.95 on 1M vectors.
+
+Workload (the Sift1M-shaped case: 1,000,000 x 128, L2): base vectors are
+integers 0..255 from a seeded 256-cluster mixture, 10,000 queries from the
+same mixture, HNSW with M=32, efConstruction=200 built once on the host
+(untimed).  A step is one batched search of the 10,000 queries: FP16
+traversal (FP32 accumulation) followed by an exact FP32 re-rank of the
+final ef candidates, at the smallest ef of the sweep 16..512 whose
+recall@10 (against exact k-NN computed on the GPU) is >= 0.95.  The plain
+FP32 traversal at the same ef is measured beside it.
+
+`--impl reference` times the FP64 CPU oracle (the plain reference this
+library is checked against) on a bounded sample of the same queries on the
+same graph, on the host cores.
+
+Multi-GPU (torchrun): every rank holds a full replica of the index and
+searches its own 10,000 queries (no data-path collective; weak scaling).
+"""
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "QPS at recall@10>=0.95, 1M vectors, 1 B300; FP16/PQ vs FP32; p99 ms"
+N_BASE, N_QUERY, DIM, M, EFC, SEED, K = 1_000_000, 10_000, 128, 32, 200, 2, 10
+EF_SWEEP = [16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512]
+WORKLOAD = ("1M x 128 integer mixture (256 clusters, values 0..255), 10k queries, L2, HNSW M=32 efC=200, "
+            "FP16 traversal + FP32 re-rank of ef, k=10")
+
+
+def rank_info():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def make_workload(n=N_BASE, nq=N_QUERY, seed=SEED):
+    from paper_2501_06121_b300 import datagen as G
+    return G.integer_mixture(n, nq, d=DIM, clusters=256, sigma=20.0, seed=seed)
+
+
+def graph_for(X, n, seed):
+    """Host HNSW build (untimed input preparation), cached on local disk so
+    that both benchmark arms on one machine share one graph."""
+    from paper_2501_06121_b300 import kann as K_
+    key = hashlib.sha1(("%d-%d-%d-%d-%d" % (n, DIM, M, EFC, seed)).encode()).hexdigest()[:12]
+    path = os.path.join(tempfile.gettempdir(), "kann_bench_graph_%s.npz" % key)
+    if os.path.exists(path):
+        z = np.load(path)
+        return {k: (z[k] if z[k].ndim else int(z[k])) for k in z.files}, 0.0, True
+    t = time.time()
+    g = K_.kann_hnsw_build_dense(X, K_.KANN_L2, M, EFC, seed, nthreads=0)
+    dt = time.time() - t
+    tmp = path + ".%d.tmp.npz" % os.getpid()
+    np.savez(tmp, **g)
+    os.replace(tmp, path)
+    return g, dt, False
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, gpu):
+        self.path = os.path.join(tempfile.gettempdir(), "kann_clocks_%d.csv" % os.getpid())
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu), "--query-gpu=" + q, "--format=csv,noheader,nounits",
+                                       "-lms", "100"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [s.strip() for s in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.remove(self.path)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def recall_at(ids, gt, k=K):
+    ids = ids[:, :k]
+    gt = gt[:, :k]
+    hit = (ids[:, :, None] == gt[:, None, :]).any(-1).sum(1)
+    return float(hit.mean() / k)
+
+
+def cpu_oracle_qps(g, X, Q, ef, seconds=12.0, threads=0):
+    """The FP64 oracle (FP16 traversal values + FP64 re-rank on FP32) on a
+    bounded sample of the queries, all host cores."""
+    import oracle as O
+    og = O.import_graph(g)
+    Xh = O.encode_f16(X)
+    ncores = os.cpu_count() or 1
+    threads = threads or ncores
+    t = time.time()
+    n0 = min(len(Q), max(threads, 16))
+    O.search_dense(og, Xh, Q[:n0], ef, ef, O.L2, dtype=O.DT_F16, nthreads=threads)
+    per = (time.time() - t) / n0
+    n = int(min(len(Q), max(n0, seconds / max(per, 1e-6))))
+    t = time.time()
+    ti, _, cnt = O.search_dense(og, Xh, Q[:n], ef, ef, O.L2, dtype=O.DT_F16, nthreads=threads)
+    O.rerank_dense(X, Q[:n], ti, K, O.L2)
+    dt = time.time() - t
+    return {"value": n / dt, "unit": "queries/s", "cores": threads, "kind": "oracle",
+            "sample": "%d of the %d queries at ef=%d (FP16 traversal values, FP64 arithmetic, FP64 re-rank), "
+                      "%.1f s" % (n, len(Q), ef, dt)}, cnt
+
+
+def run_reference(args):
+    r, world, _ = rank_info()
+    if r != 0:
+        return
+    X, Q = make_workload()
+    g, _, _ = graph_for(X, N_BASE, SEED)
+    ef = args.ef or 64
+    for _ in range(args.warmup):
+        pass
+    total_q, total_t = 0, 0.0
+    base = None
+    for _ in range(max(1, args.steps)):
+        cb, _ = cpu_oracle_qps(g, X, Q, ef, seconds=max(2.0, 60.0 / max(1, args.steps)))
+        base = cb
+        n = int(cb["sample"].split(" of ")[0])
+        total_q += n
+        total_t += n / cb["value"]
+    v = total_q / total_t
+    base["value"] = v
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "queries/s", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * total_t / max(1, args.steps), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "ef": ef, "k": K, "sample": base["sample"]},
+           "cpu_baseline": base, "e2e": {"value": v, "unit": "queries/s", "h2d_bytes_per_step": 0,
+                                         "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def traffic_from_profiles(kernel_sha):
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            t = json.load(f)
+        if t.get("kernel_source_sha1") == kernel_sha:
+            return t.get("dram_bytes_per_launch")
+    except Exception:
+        pass
+    return None
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--ef", type=int, default=0, help="fix ef instead of sweeping")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    from paper_2501_06121_b300 import build as lib_build
+    from paper_2501_06121_b300 import kann as K_
+
+    rank, world, local = rank_info()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    lib_build.build()
+    dev = torch.device("cuda", local)
+
+    # ---- inputs (untimed)
+    X, Q = make_workload(seed=SEED)
+    if world > 1:
+        Q = make_workload(n=1, nq=N_QUERY * world, seed=SEED)[1][rank * N_QUERY:(rank + 1) * N_QUERY]
+    t0 = time.time()
+    if world > 1 and rank != 0:
+        dist.barrier()
+    g, build_s, cached = graph_for(X, N_BASE, SEED)
+    if world > 1 and rank == 0:
+        dist.barrier()
+    Xd = torch.from_numpy(X).to(dev)
+    Xh, _ = K_.kann_quantize(Xd, K_.KANN_F16)
+    gd = K_.graph_to_device(g, dev)
+    idx16 = K_.kann_index_upload(gd, vectors=Xh, dtype=K_.KANN_F16, metric=K_.KANN_L2, rerank=Xd)
+    idx32 = K_.kann_index_upload(gd, vectors=Xd, dtype=K_.KANN_F32, metric=K_.KANN_L2)
+    Qd = torch.from_numpy(Q).to(dev)
+    gt, _ = K_.kann_exact_knn(Qd, Xd, K, K_.KANN_L2)
+    torch.cuda.synchronize()
+    gt = gt.cpu().numpy()
+
+    # ---- ef sweep: smallest ef with recall@10 >= 0.95 (FP16 + re-rank)
+    sweep = {}
+    ef_sel = args.ef or None
+    for ef in ([args.ef] if args.ef else EF_SWEEP):
+        ids, _ = K_.kann_search_ex(idx16, Qd, K, ef, rerank=-1)
+        torch.cuda.synchronize()
+        rec = recall_at(ids.cpu().numpy(), gt)
+        i32, _ = K_.kann_search_ex(idx32, Qd, K, ef)
+        torch.cuda.synchronize()
+        sweep[ef] = {"recall_fp16_rerank": rec, "recall_fp32": recall_at(i32.cpu().numpy(), gt)}
+        if ef_sel is None and rec >= 0.95:
+            ef_sel = ef
+            break
+    if ef_sel is None:
+        ef_sel = EF_SWEEP[-1]
+    ef = ef_sel
+
+    # algorithmic work per query (large visited table: no repeated distances)
+    cnt = torch.zeros((N_QUERY, 4), dtype=torch.int32, device=dev)
+    K_.kann_search_ex(idx16, Qd, K, ef, rerank=-1, counters=cnt, hash_bits=14)
+    torch.cuda.synchronize()
+    c = cnt.double().mean(0).cpu().numpy()
+    row16, row32 = DIM * 2, DIM * 4
+    bytes_per_q = (c[0] * row16 + c[1] * 2 * M * 4 + c[2] * row16 + c[3] * M * 4 + ef * row32
+                   + DIM * 4 + K * 8)
+
+    stream = torch.cuda.current_stream()
+
+    def step(index, rr):
+        return K_.kann_search_ex(index, Qd, K, ef, rerank=rr)
+
+    ids_buf = torch.empty((N_QUERY, K), dtype=torch.int32, device=dev)
+    d_buf = torch.empty((N_QUERY, K), dtype=torch.float32, device=dev)
+
+    def timed(index, rr, steps, warm):
+        for _ in range(warm):
+            K_.kann_search_ex(index, Qd, K, ef, ids=ids_buf, dists=d_buf, rerank=rr)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+        evs[0].record(stream)
+        for i in range(steps):
+            K_.kann_search_ex(index, Qd, K, ef, ids=ids_buf, dists=d_buf, rerank=rr)
+            evs[i + 1].record(stream)
+        torch.cuda.synchronize()
+        per = [evs[i].elapsed_time(evs[i + 1]) for i in range(steps)]
+        return sum(per), per
+
+    clocks = Clocks(local)
+    total_ms, per = timed(idx16, -1, args.steps, args.warmup)
+    clk = clocks.stop()
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    fp32_ms, _ = timed(idx32, 0, max(3, args.steps // 2), 2)
+    fp32_ms /= max(3, args.steps // 2)
+
+    qps = world * N_QUERY * args.steps / (total_ms / 1e3)
+    ms_step = total_ms / args.steps
+    per_launch_s = ms_step / 1e3
+    achieved = N_QUERY * bytes_per_q / per_launch_s / 1e9
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except Exception:
+        pass
+    hbm = peaks.get("hbm_gbs", 6400.0)
+    with open(os.path.join(ROOT, "paper_2501_06121_b300", "csrc", "kann_search.cu"), "rb") as f:
+        ksha = hashlib.sha1(f.read()).hexdigest()
+    traffic = traffic_from_profiles(ksha)
+
+    # ---- end to end through the public API with host buffers
+    Qpin = torch.from_numpy(Q).pin_memory()
+    ids_h = torch.empty((N_QUERY, K), dtype=torch.int32).pin_memory()
+    d_h = torch.empty((N_QUERY, K), dtype=torch.float32).pin_memory()
+    Qdev = torch.empty_like(Qd)
+
+    def e2e_step():
+        Qdev.copy_(Qpin, non_blocking=True)
+        K_.kann_search_ex(idx16, Qdev, K, ef, ids=ids_buf, dists=d_buf, rerank=-1)
+        ids_h.copy_(ids_buf, non_blocking=True)
+        d_h.copy_(d_buf, non_blocking=True)
+
+    for _ in range(args.warmup):
+        e2e_step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_qps = world * N_QUERY * args.steps / (e2e_ms / 1e3)
+    final_recall = recall_at(ids_buf.cpu().numpy(), gt)
+
+    cpu_base = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu_base, _ = cpu_oracle_qps(g, X, Q, ef)
+
+    if rank == 0:
+        per_sorted = sorted(per)
+        out = {
+            "metric": METRIC, "value": qps, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "ef": ef, "k": K, "recall@10": final_recall,
+                       "storage": "f16 traversal + f32 re-rank (R = ef)", "parallelism": "replicas%d" % world,
+                       "l2": "inputs larger than L2 (f16 base 256 MB + f32 base 512 MB + graph 256 MB)",
+                       "fp32_plain_qps": N_QUERY * world / (fp32_ms / 1e3), "fp32_plain_ms_per_step": fp32_ms,
+                       "ef_sweep": sweep, "graph_build_s": build_s, "graph_cached": cached,
+                       "batch_latency_ms": {"p50": per_sorted[len(per) // 2],
+                                            "p99": per_sorted[min(len(per) - 1, int(0.99 * len(per)))]},
+                       "work_per_query": {"l0_dist": c[0], "l0_expansions": c[1], "upper_dist": c[2],
+                                          "upper_hops": c[3]},
+                       "host_cores": os.cpu_count()},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                         "traffic": traffic, "algorithmic_bytes_per_query": bytes_per_q,
+                         "kernel": "search_dense_kernel<f16> (one launch per step)",
+                         "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured copy)" if peaks else "fallback"},
+            "e2e": {"value": e2e_qps, "unit": "queries/s", "h2d_bytes_per_step": int(Q.nbytes),
+                    "d2h_bytes_per_step": int(ids_h.numel() * 4 + d_h.numel() * 4)},
+            "gpu_launches": args.steps,
+            "clocks": clk,
+            "cpu_baseline": cpu_base,
+        }
+        print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

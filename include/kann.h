@@ -1,0 +1,239 @@
+/*
+ * kann.h -- C ABI of the B300 (sm_103a) batched HNSW search library.
+ *
+ * The library runs the query-time path of the composable ANN method of
+ * kANNolo (Delfino et al., 2025): k-NN search ("identify the k nearest
+ * neighbors to a given query point", Sec. 1) over an HNSW graph (Sec. 2,
+ * citing Malkov & Yashunin) whose items are dense vectors (L2 or inner
+ * product), Product-Quantization codes (Sec. 2, citing Jegou et al.) or
+ * sparse term/weight vectors (Sec. 3, Table 1).
+ *
+ * Conventions shared by every call:
+ *   - Every call returns an int status (KANN_OK = 0 or a KANN_E* code);
+ *     kann_status_str() names it.  Nothing is launched when a call fails
+ *     argument validation.
+ *   - Distances are "smaller is better": L2 = sum (q - x)^2 (squared, no
+ *     root), IP = -sum q * x.  Results are ordered by the total order on
+ *     (distance, id): distance first (NaN counts as +inf), then id.
+ *   - Pointers named d_* are DEVICE pointers owned by the caller.  The index
+ *     borrows them: the caller keeps them alive and unchanged until
+ *     kann_index_destroy().  The index owns only a small host-side record.
+ *   - Pointers named h_* are HOST pointers, read or written before the call
+ *     returns.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Search and exact-k-NN calls are asynchronous on it; the only
+ *     host synchronisation is inside kann_index_upload's validation.
+ *   - Integer ids are int32 (n < 2^31).  Missing results are id -1 with
+ *     distance +inf.
+ */
+#ifndef KANN_H
+#define KANN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes -------------------------------------------------------*/
+#define KANN_OK 0
+#define KANN_EINVAL 1   /* bad argument (null pointer, size, k/ef range, alignment) */
+#define KANN_ENOMEM 2   /* a host allocation or the shared-memory budget failed */
+#define KANN_ECUDA 3    /* a CUDA runtime call failed; see kann_last_cuda_error() */
+#define KANN_EFORMAT 4  /* graph/vector description is inconsistent (ids out of range, degree caps) */
+#define KANN_ETIMEOUT 5 /* a bounded device wait ran out */
+
+/* ---- per-query status bits (optional d_status output of kann_search_ex) -*/
+#define KANN_QSTAT_HOPCAP 1u    /* layer-0 expansions hit opts.max_hops; result is the W reached */
+#define KANN_QSTAT_FORGOT 2u    /* the visited table was cleared at least once (results unaffected) */
+#define KANN_QSTAT_BAD_ID 4u    /* an adjacency entry >= n was met and skipped */
+
+/* ---- enums --------------------------------------------------------------*/
+#define KANN_L2 0
+#define KANN_IP 1
+
+#define KANN_F32 0   /* IEEE binary32 */
+#define KANN_F16 1   /* IEEE binary16, round-to-nearest-even from FP32 */
+#define KANN_BF16 2  /* bfloat16, round-to-nearest-even from FP32 */
+#define KANN_E4M3 3  /* OCP FP8 E4M3 with a per-vector FP32 scale s: x = s * code */
+
+/* Search limits of this build. */
+#define KANN_MAX_EF 1024    /* ef_eff = max(ef, k) must not exceed this */
+#define KANN_MAX_M0 64      /* layer-0 degree cap (M0 = 2M, so M <= 32) */
+#define KANN_MAX_DIM 4096   /* dense dimension */
+
+/* ---- index descriptions -------------------------------------------------*/
+
+/* The HNSW graph (Malkov & Yashunin), serialised with fixed-width rows.
+ *   d_level      [n] int8      level of each node (0 = layer 0 only)
+ *   d_l0         [n][M0] int32 layer-0 neighbours, -1 padded
+ *   d_upper_slot [n] int32     row of the node in d_upper, -1 if level 0
+ *   d_upper      [n_upper][max_level][M] int32, layer l at index l - 1,
+ *                -1 padded (may be NULL when max_level == 0)
+ * entry is the entry point (a node of level max_level). */
+typedef struct {
+  int64_t n;
+  int32_t M;
+  int32_t M0;
+  int32_t max_level;
+  int32_t entry;
+  int64_t n_upper;
+  const int8_t* d_level;
+  const int32_t* d_l0;
+  const int32_t* d_upper_slot;
+  const int32_t* d_upper;
+} kann_graph_desc;
+
+/* Dense vectors [n][d] in `dtype`, rows `row_stride_bytes` apart (a multiple
+ * of 16, >= d * element size; d * element size must itself be a multiple of
+ * 16).  d_scale [n] FP32 is required for KANN_E4M3 and ignored otherwise. */
+typedef struct {
+  int32_t dtype;
+  int32_t d;
+  int32_t metric;
+  int32_t reserved;
+  const void* d_data;
+  const float* d_scale;
+  int64_t row_stride_bytes;
+} kann_vectors_desc;
+
+/* Product quantization (Jegou et al.): m subspaces of dsub dims, ksub = 256
+ * centroids each; d_codes [n][m] uint8, d_codebooks [m][256][dsub] FP32.
+ * The ADC distance is sum_j LUT[j][code_j] with the per-query table LUT built
+ * on the device for `metric`. */
+typedef struct {
+  int32_t m;
+  int32_t ksub;
+  int32_t dsub;
+  int32_t metric;
+  const uint8_t* d_codes;
+  const float* d_codebooks;
+} kann_pq_desc;
+
+/* Sparse vectors in CSR: d_indptr [n+1] int64, d_terms [nnz] uint16 sorted
+ * and unique within a row, d_weights [nnz] FP32; term ids < vocab.
+ * Measure: IP (distance = -sum over shared terms of w_q * w_x). */
+typedef struct {
+  const int64_t* d_indptr;
+  const uint16_t* d_terms;
+  const float* d_weights;
+  int32_t vocab;
+  int32_t reserved;
+} kann_sparse_desc;
+
+typedef struct kann_index kann_index_t;
+
+/* Build a device-resident index from caller-owned device arrays (Sec. 2:
+ * the Dataset "provides access to the data", the index "pinpoints which
+ * vector shall be compared with the query").  Exactly one traversal source
+ * must be given: `v` (dense), `pq`, or `sp`.  `rerank` (nullable) is a dense
+ * KANN_F32 copy of the same items with the same d and metric, used for exact
+ * re-ranking of reduced-precision traversal.  The graph's metadata and
+ * degree caps are validated on the host; with `validate_ids` != 0 the
+ * adjacency arrays are also scanned on the device for ids outside [0, n)
+ * (one synchronising call).  On success *out owns a host record only.
+ * Errors: KANN_EINVAL (nulls, sizes, alignment), KANN_EFORMAT (metadata or
+ * ids inconsistent), KANN_ECUDA, KANN_ENOMEM. */
+int kann_index_upload(kann_index_t** out, const kann_graph_desc* g, const kann_vectors_desc* v,
+                      const kann_pq_desc* pq, const kann_sparse_desc* sp, const kann_vectors_desc* rerank,
+                      int validate_ids);
+
+/* Release the host record.  Borrowed device arrays are untouched. */
+int kann_index_destroy(kann_index_t* idx);
+
+/* Optional search settings (zero-initialise, then set what is needed). */
+typedef struct {
+  int32_t rerank;          /* 0: no re-rank; R > 0: re-rank the best min(R, |W|) traversal
+                              candidates exactly in FP32 from the index's rerank copy;
+                              -1: R = ef_eff.  R must be >= k. */
+  int32_t max_hops;        /* cap on layer-0 expansions per query; 0 = 1,000,000 */
+  int32_t hash_bits;       /* log2 of the per-query visited table; 0 = automatic */
+  int32_t warps_per_block; /* queries per CTA (one warp each); 0 = automatic */
+  uint32_t* d_status;      /* [n] per-query KANN_QSTAT_* bits, nullable */
+  int32_t* d_counters;     /* [n][4] per-query counters, nullable: layer-0 distance
+                              evaluations, layer-0 expansions, upper-layer distance
+                              evaluations, upper-layer hops */
+} kann_search_opts;
+
+/* HNSW K-NN-SEARCH (Malkov & Yashunin Alg. 5) for n dense FP32 queries
+ * d_queries [n][d]: greedy descent from the entry point through layers
+ * max_level..1, then the ef-bounded beam on layer 0 (ef_eff = max(ef, k)),
+ * one expansion per step in (distance, id) order, then the k best.
+ * Outputs d_ids [n][k] int32 and d_dists [n][k] FP32.  For a PQ index the
+ * queries are the raw FP32 vectors (d = m * dsub) and the per-query ADC
+ * table is built on the device.  n == 0 is a no-op.
+ * Errors: KANN_EINVAL (k < 1, ef_eff > KANN_MAX_EF, sparse index, nulls). */
+int kann_search(const kann_index_t* idx, const float* d_queries, int n, int k, int ef, int32_t* d_ids,
+                float* d_dists, void* stream);
+
+/* kann_search with options (re-rank, status, counters, tuning). */
+int kann_search_ex(const kann_index_t* idx, const float* d_queries, int n, int k, int ef, int32_t* d_ids,
+                   float* d_dists, const kann_search_opts* opts, void* stream);
+
+/* Mixed batch: query i uses k = d_k[i] and ef = d_ef[i] (both device int32
+ * arrays; 1 <= k <= kmax, ef_eff <= efmax).  Outputs are [n][kmax]; entries
+ * past query i's k are id -1 / +inf.  Same search as kann_search_ex. */
+int kann_search_batch(const kann_index_t* idx, const float* d_queries, int n, const int32_t* d_k,
+                      const int32_t* d_ef, int kmax, int efmax, int32_t* d_ids, float* d_dists,
+                      const kann_search_opts* opts, void* stream);
+
+/* Sparse-query search over a sparse index: queries in CSR (d_q_indptr [n+1]
+ * int64, d_q_terms uint16 sorted unique per row, d_q_weights FP32). */
+int kann_search_sparse(const kann_index_t* idx, const int64_t* d_q_indptr, const uint16_t* d_q_terms,
+                       const float* d_q_weights, int n, int k, int ef, int32_t* d_ids, float* d_dists,
+                       const kann_search_opts* opts, void* stream);
+
+/* Exact k-NN by brute force (the ground truth recall is measured against):
+ * d_queries [nq][d] and d_base [nb][d], both in `dtype` (KANN_F32 or
+ * KANN_BF16 / KANN_F16 for the tensor-core path), row-major, contiguous.
+ * Scores for L2 are ||x||^2 - 2 q.x (+ ||q||^2) accumulated in FP32; the k best
+ * per query are returned sorted by (distance, id) in d_ids / d_dists.
+ * d_ws is caller-owned device scratch of at least
+ * kann_exact_knn_workspace_bytes(...) bytes.  Errors: KANN_EINVAL. */
+int kann_exact_knn(const void* d_queries, const void* d_base, int nq, int64_t nb, int d, int metric, int dtype,
+                   int k, int32_t* d_ids, float* d_dists, void* d_ws, size_t ws_bytes, void* stream);
+
+size_t kann_exact_knn_workspace_bytes(int nq, int64_t nb, int d, int k, int dtype);
+
+/* Convert FP32 rows d_x [n][d] to a storage format on the device:
+ * KANN_F16 / KANN_BF16 (round to nearest even) into d_out [n][d] 16-bit, or
+ * KANN_E4M3 with per-row scale s = max|x| / 448 (FP32 division) and codes
+ * RNE_satfinite(x / s) into d_out [n][d] uint8 and d_scale [n] (an all-zero
+ * row gets s = 0 and zero codes).  Asynchronous on `stream`. */
+int kann_quantize(const float* d_x, int64_t n, int d, int dtype, void* d_out, float* d_scale, void* stream);
+
+/* ---- graph construction (host, multi-threaded) ---------------------------
+ * The indexing pipeline of the paper (Sec. 2, Fig. 1) ends in an HNSW graph;
+ * search treats it as a fixed input.  These host calls build one in the
+ * serialised layout above from FP32 dense rows h_x [n][d] or a CSR sparse set.
+ *
+ * kann_hnsw_levels: the level of every node, level = floor(-ln U / ln M)
+ * with U in (0, 1] from a counter-based SplitMix64 draw keyed by (seed, id);
+ * writes h_level [n] and returns max_level and n_upper for sizing.
+ *
+ * kann_hnsw_build_dense / _sparse: insert ids 0..n-1 with `nthreads` threads
+ * (0 = all cores), Malkov & Yashunin's neighbour-selection heuristic, degree
+ * caps M (upper layers) and 2M (layer 0).  Output arrays are caller-owned
+ * host buffers sized by kann_hnsw_levels: h_l0 [n][2M], h_upper_slot [n],
+ * h_upper [n_upper][max_level][M]; *h_entry receives the entry point. */
+int kann_hnsw_levels(int64_t n, int M, uint64_t seed, int8_t* h_level, int32_t* h_max_level, int64_t* h_n_upper);
+
+int kann_hnsw_build_dense(const float* h_x, int64_t n, int d, int metric, int M, int ef_construction, uint64_t seed,
+                          int nthreads, const int8_t* h_level, int32_t* h_l0, int32_t* h_upper_slot,
+                          int32_t* h_upper, int32_t* h_entry);
+
+int kann_hnsw_build_sparse(const int64_t* h_indptr, const uint16_t* h_terms, const float* h_weights, int64_t n,
+                           int M, int ef_construction, uint64_t seed, int nthreads, const int8_t* h_level,
+                           int32_t* h_l0, int32_t* h_upper_slot, int32_t* h_upper, int32_t* h_entry);
+
+/* ---- diagnostics --------------------------------------------------------*/
+const char* kann_status_str(int status);
+/* The cudaError_t of the most recent failed CUDA call in this thread. */
+int kann_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KANN_H */

@@ -1,0 +1,67 @@
+// kann_internal.h -- definitions shared by the library's translation units.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/kann.h"
+
+namespace kann {
+
+// Arguments of one dense/PQ search launch (all device pointers).
+struct SearchArgs {
+  // graph (HNSW, fixed-width rows)
+  const int32_t* l0;
+  const int32_t* upper_slot;
+  const int32_t* upper;
+  int64_t n;
+  int M0, M, max_level, entry;
+  // traversal rows
+  const unsigned char* data;
+  int64_t stride;
+  const float* scale;
+  int d, nchunks, lpr, metric;
+  // PQ traversal
+  const unsigned char* codes;
+  const float* codebooks;
+  int pq_m, pq_dsub;
+  // re-rank rows (FP32)
+  const unsigned char* rr_data;
+  int64_t rr_stride;
+  int rr_nchunks, rr_lpr, R;
+  // queries and outputs
+  const float* q;
+  int nq, k, ef, kmax, efmax;
+  const int32_t* k_arr;
+  const int32_t* ef_arr;
+  int32_t* out_ids;
+  float* out_d;
+  uint32_t* status;
+  int32_t* counters;
+  int hbits, max_hops;
+  int efcap;       // W capacity (power of two >= efmax, >= 32)
+  int warp_smem;   // bytes of shared memory per warp
+};
+
+// Sparse search additions.
+struct SparseArgs {
+  const int64_t* indptr;
+  const uint16_t* terms;
+  const float* w;
+  const int64_t* q_indptr;
+  const uint16_t* q_terms;
+  const float* q_w;
+  int vocab;
+};
+
+// Per-warp shared memory needed by a dense search with these settings.
+int search_warp_smem(int efcap, int hbits);
+int search_warp_smem_pq(int efcap, int hbits, int m);
+
+// Launchers (kann_search.cu); return a cudaError_t.
+int launch_search_dense(const SearchArgs& a, int dtype, int wpb, void* stream);
+int launch_search_pq(const SearchArgs& a, int wpb, void* stream);
+int launch_search_sparse(const SearchArgs& a, const SparseArgs& s, int wpb, void* stream);
+
+void set_cuda_error(int e);
+
+}  // namespace kann

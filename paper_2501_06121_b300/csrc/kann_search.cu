@@ -1,0 +1,529 @@
+// kann_search.cu -- batched HNSW search kernels for sm_103a.
+//
+// One warp searches one query (HNSW K-NN-SEARCH, Malkov & Yashunin Alg. 5,
+// the index of kANNolo Sec. 2):
+//   1. distance to the entry point;
+//   2. greedy descent through layers max_level..1: move to the (d, id)-best
+//      neighbour while it beats the current node (SEARCH-LAYER with ef = 1);
+//   3. layer-0 beam: W, the ef best (d, id) keys found so far, sorted, each
+//      with an "expanded" bit.  Each step expands the best unexpanded entry:
+//      its adjacency row (M0 ids) is read with one coalesced load per lane,
+//      ids already in the visited table are dropped, the surviving rows are
+//      gathered with 16-byte loads (several rows in flight per warp) and their
+//      distances reduced with shuffles; keys that beat worst(W) are sorted by a
+//      warp bitonic network and merged into W in place (rank by binary search,
+//      move right-to-left).  The search ends when W has no unexpanded entry.
+//      This is the two-heap SEARCH-LAYER (Alg. 2) in its flag-buffer form; both
+//      give the same W under the (d, id) total order;
+//   4. optional exact FP32 re-rank of the best R entries of W;
+//   5. the k best keys are written out (id -1 / +inf padding).
+//
+// The visited table is a per-warp open-addressing hash in shared memory.  It
+// may forget (it is cleared and refilled with W's ids when half full, and an
+// id that finds no slot within the probe window is not stored) but it never
+// reports an unvisited id as visited.  Forgetting is harmless because an id
+// already in W is never inserted twice (equal keys are detected in the merge),
+// and an id that left W or was rejected is worse than worst(W), which only
+// improves once W is full; the search therefore returns the same W as with an
+// exact visited set.  Forgotten ids cost only a repeated distance.
+#include "kann_device.cuh"
+#include "kann_internal.h"
+
+namespace kann {
+namespace {
+
+constexpr u64 FLAG = 0x80000000ull;  // "expanded" bit, kept in the id word
+constexpr uint32_t HEMPTY = 0xffffffffu;
+constexpr int HASH_MAX_PROBE = 32;
+
+__device__ __forceinline__ u64 kmask(u64 k) { return k & ~FLAG; }
+__device__ __forceinline__ uint32_t key_id(u64 k) { return (uint32_t)k & 0x7fffffffu; }
+
+// Visited table.  Returns 0 if id is present, 1 if it was inserted now, 2 if
+// it is absent but the probe window is full (treated as unvisited, not stored).
+__device__ __forceinline__ int visit(uint32_t* H, int hbits, uint32_t id) {
+  const uint32_t mask = (1u << hbits) - 1u;
+  uint32_t h = (id * 2654435761u) >> (32 - hbits);
+  volatile uint32_t* vh = H;
+  for (int p = 0; p < HASH_MAX_PROBE; ++p) {
+    uint32_t v = vh[h];
+    if (v == id) return 0;
+    if (v == HEMPTY) {
+      uint32_t old = atomicCAS(&H[h], HEMPTY, id);
+      if (old == HEMPTY) return 1;
+      if (old == id) return 0;
+    }
+    h = (h + 1u) & mask;
+  }
+  return 2;
+}
+
+__device__ __forceinline__ int lower_bound_w(const u64* W, int len, u64 key) {
+  int lo = 0, hi = len;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (kmask(W[mid]) < key) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// number of entries of the ascending array A[0..n) that are <= x
+__device__ __forceinline__ int count_le(const int* A, int n, int x) {
+  int lo = 0, hi = n;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (A[mid] <= x) lo = mid + 1;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// ---------------------------------------------------------------------------
+// Dense back-end: rows of `DT` elements; lanes are split into groups of `lpr`
+// lanes per row, lane `sub` of a group owning 16-byte chunks sub, sub + lpr,
+// ...  (CPL chunks at most).  The query's matching chunks stay in registers.
+// U row-batches are loaded before any is consumed, so U * 32 / lpr rows are
+// in flight per warp.  The summation order of a row's distance depends only
+// on the row, never on its slot in the batch.
+// ---------------------------------------------------------------------------
+template <int DT, int CPL>
+struct DenseBackend {
+  static constexpr int EPC = Fmt<DT>::EPC;
+  static constexpr int U = (8 / CPL) > 0 ? (8 / CPL) : 1;
+  float qr[CPL][EPC];
+
+  __device__ __forceinline__ void init(const SearchArgs& a, int qi, int lane, unsigned char*) {
+    const float* q = a.q + (size_t)qi * a.d;
+    const int sub = lane & (a.lpr - 1);
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) {
+      const int ch = sub + c * a.lpr;
+#pragma unroll
+      for (int e4 = 0; e4 < EPC / 4; ++e4) {
+        float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (ch < a.nchunks) t = __ldg(reinterpret_cast<const float4*>(q + ch * EPC) + e4);
+        qr[c][4 * e4 + 0] = t.x;
+        qr[c][4 * e4 + 1] = t.y;
+        qr[c][4 * e4 + 2] = t.z;
+        qr[c][4 * e4 + 3] = t.w;
+      }
+    }
+  }
+
+  __device__ __forceinline__ void dists(const SearchArgs& a, const int* cid, int cnt, u64* ck, int lane) {
+    const int lpr = a.lpr, rpi = 32 / lpr;
+    const int sub = lane & (lpr - 1), grp = lane / lpr;
+    for (int base = 0; base < cnt; base += rpi * U) {
+      uint4 buf[U][CPL];
+      float sc[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int r = base + u * rpi + grp;
+        const int id = r < cnt ? cid[r] : -1;
+        const unsigned char* row = a.data + (int64_t)(id < 0 ? 0 : id) * a.stride;
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) {
+          const int ch = sub + c * lpr;
+          buf[u][c] = (id >= 0 && ch < a.nchunks) ? ldg_stream16(row + ch * 16) : make_uint4(0u, 0u, 0u, 0u);
+        }
+        sc[u] = 1.f;
+        if (DT == KANN_E4M3) sc[u] = id >= 0 ? __ldg(a.scale + id) : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int r = base + u * rpi + grp;
+        float acc = 0.f;
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) {
+          float x[EPC];
+          Fmt<DT>::unpack(buf[u][c], x);
+#pragma unroll
+          for (int e = 0; e < EPC; ++e) {
+            const float xv = (DT == KANN_E4M3) ? x[e] * sc[u] : x[e];
+            if (a.metric == KANN_L2) {
+              const float t = qr[c][e] - xv;
+              acc = fmaf(t, t, acc);
+            } else {
+              acc = fmaf(qr[c][e], xv, acc);
+            }
+          }
+        }
+        for (int o = lpr >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
+        if (sub == 0 && r < cnt) ck[r] = make_key(a.metric == KANN_L2 ? acc : -acc, (uint32_t)cid[r]);
+      }
+    }
+  }
+};
+
+// Exact FP32 distances for the re-rank, from the index's FP32 copy.  Same
+// lane/chunk mapping and summation order as the FP32 dense back-end, so a
+// re-ranked distance is bit-identical to the FP32 traversal distance.
+template <int CPL>
+__device__ __forceinline__ void rerank_dists(const SearchArgs& a, const float* q, const int* cid, int cnt, u64* ck,
+                                             int lane) {
+  constexpr int U = (8 / CPL) > 0 ? (8 / CPL) : 1;
+  const int lpr = a.rr_lpr, rpi = 32 / lpr;
+  const int sub = lane & (lpr - 1), grp = lane / lpr;
+  float4 qv[CPL];
+#pragma unroll
+  for (int c = 0; c < CPL; ++c) {
+    const int ch = sub + c * lpr;
+    qv[c] = ch < a.rr_nchunks ? __ldg(reinterpret_cast<const float4*>(q) + ch) : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  for (int base = 0; base < cnt; base += rpi * U) {
+    uint4 buf[U][CPL];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int r = base + u * rpi + grp;
+      const int id = r < cnt ? cid[r] : -1;
+      const unsigned char* row = a.rr_data + (int64_t)(id < 0 ? 0 : id) * a.rr_stride;
+#pragma unroll
+      for (int c = 0; c < CPL; ++c) {
+        const int ch = sub + c * lpr;
+        buf[u][c] = (id >= 0 && ch < a.rr_nchunks) ? ldg_stream16(row + ch * 16) : make_uint4(0u, 0u, 0u, 0u);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int r = base + u * rpi + grp;
+      float acc = 0.f;
+#pragma unroll
+      for (int c = 0; c < CPL; ++c) {
+        const float x[4] = {__uint_as_float(buf[u][c].x), __uint_as_float(buf[u][c].y),
+                            __uint_as_float(buf[u][c].z), __uint_as_float(buf[u][c].w)};
+        const float qq[4] = {qv[c].x, qv[c].y, qv[c].z, qv[c].w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          if (a.metric == KANN_L2) {
+            const float t = qq[e] - x[e];
+            acc = fmaf(t, t, acc);
+          } else {
+            acc = fmaf(qq[e], x[e], acc);
+          }
+        }
+      }
+      for (int o = lpr >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
+      if (sub == 0 && r < cnt) ck[r] = make_key(a.metric == KANN_L2 ? acc : -acc, (uint32_t)cid[r]);
+    }
+  }
+}
+
+// Shared memory of one warp: W[efcap] keys, candidate keys[64], candidate
+// ids[64], candidate W-ranks[64], then the visited table (1 << hbits words),
+// then back-end scratch.
+struct WarpSmem {
+  u64* W;
+  u64* ck;
+  int* cid;
+  int* clb;
+  uint32_t* H;
+  unsigned char* extra;
+  __device__ __forceinline__ WarpSmem(unsigned char* ws, int efcap, int hbits) {
+    W = reinterpret_cast<u64*>(ws);
+    ck = W + efcap;
+    cid = reinterpret_cast<int*>(ck + 64);
+    clb = cid + 64;
+    H = reinterpret_cast<uint32_t*>(clb + 64);
+    extra = reinterpret_cast<unsigned char*>(H + (1 << hbits));
+  }
+};
+
+template <class B, int CPLR>
+__device__ __forceinline__ void search_one(const SearchArgs& a, B& be, int qi, int lane, unsigned char* ws) {
+  WarpSmem s(ws, a.efcap, a.hbits);
+  u64* W = s.W;
+  u64* ck = s.ck;
+  int* cid = s.cid;
+  int* clb = s.clb;
+  uint32_t* H = s.H;
+  const int Hn = 1 << a.hbits;
+  const unsigned lt = (1u << lane) - 1u;
+
+  int k = a.k, ef = a.ef;
+  if (a.k_arr) {
+    k = min(max(a.k_arr[qi], 1), a.kmax);
+    ef = a.ef_arr[qi];
+  }
+  ef = min(max(ef, k), a.efmax);
+  uint32_t st = 0;
+  int c_l0d = 0, c_l0e = 0, c_upd = 0, c_uph = 0;
+
+  be.init(a, qi, lane, s.extra);
+
+  // 1. entry point
+  if (lane == 0) cid[0] = a.entry;
+  __syncwarp();
+  be.dists(a, cid, 1, ck, lane);
+  __syncwarp();
+  u64 cur = ck[0];
+  c_upd = 1;
+  __syncwarp();
+
+  // 2. greedy descent through the upper layers
+  for (int l = a.max_level; l >= 1; --l) {
+    for (;;) {
+      const int cur_id = (int)key_id(cur);
+      const int slot = __ldg(a.upper_slot + cur_id);
+      int v = -1;
+      if (slot >= 0 && lane < a.M) v = __ldg(a.upper + ((int64_t)slot * a.max_level + (l - 1)) * a.M + lane);
+      if (slot < 0 || v >= a.n) st |= KANN_QSTAT_BAD_ID;
+      if (v >= a.n) v = -1;
+      const bool ok = v >= 0;
+      const unsigned bal = __ballot_sync(FULL, ok);
+      const int cnt = __popc(bal);
+      if (ok) cid[__popc(bal & lt)] = v;
+      __syncwarp();
+      be.dists(a, cid, cnt, ck, lane);
+      __syncwarp();
+      c_upd += cnt;
+      ++c_uph;
+      const u64 best = warp_min64(lane < cnt ? ck[lane] : KEY_MAX);
+      __syncwarp();
+      if (best < cur) cur = best;
+      else break;
+    }
+  }
+
+  // 3. layer-0 beam
+  for (int i = lane; i < Hn; i += 32) H[i] = HEMPTY;
+  __syncwarp();
+  if (lane == 0) {
+    visit(H, a.hbits, key_id(cur));
+    W[0] = cur;
+  }
+  __syncwarp();
+  int len = 1, cursor = 0, hops = 0, stored = 1;
+  for (;;) {
+    int p = -1;
+    for (int b = cursor; b < len; b += 32) {
+      const int i = b + lane;
+      const bool un = i < len && !(W[i] & FLAG);
+      const unsigned m = __ballot_sync(FULL, un);
+      if (m) {
+        p = b + __ffs(m) - 1;
+        break;
+      }
+    }
+    if (p < 0) break;
+    if (hops >= a.max_hops) {
+      st |= KANN_QSTAT_HOPCAP;
+      break;
+    }
+    ++hops;
+    const u64 ce = W[p];
+    __syncwarp();
+    if (lane == 0) W[p] = ce | FLAG;
+    cursor = p + 1;
+    const int c_id = (int)key_id(ce);
+    const int32_t* nb = a.l0 + (int64_t)c_id * a.M0;
+    int v0 = lane < a.M0 ? __ldg(nb + lane) : -1;
+    int v1 = lane + 32 < a.M0 ? __ldg(nb + 32 + lane) : -1;
+    if (v0 >= a.n || v1 >= a.n) st |= KANN_QSTAT_BAD_ID;
+    if (v0 >= a.n) v0 = -1;
+    if (v1 >= a.n) v1 = -1;
+    const int r0 = v0 >= 0 ? visit(H, a.hbits, (uint32_t)v0) : 0;
+    const int r1 = v1 >= 0 ? visit(H, a.hbits, (uint32_t)v1) : 0;
+    stored += __popc(__ballot_sync(FULL, r0 == 1)) + __popc(__ballot_sync(FULL, r1 == 1));
+    const unsigned b0 = __ballot_sync(FULL, r0 != 0), b1 = __ballot_sync(FULL, r1 != 0);
+    const int c0 = __popc(b0), cnt = c0 + __popc(b1);
+    if (r0) cid[__popc(b0 & lt)] = v0;
+    if (r1) cid[c0 + __popc(b1 & lt)] = v1;
+    __syncwarp();
+    ++c_l0e;
+    if (cnt > 0) {
+      be.dists(a, cid, cnt, ck, lane);
+      __syncwarp();
+      c_l0d += cnt;
+      const u64 worst = len >= ef ? kmask(W[len - 1]) : KEY_MAX;
+      u64 e0 = lane < cnt ? ck[lane] : KEY_MAX;
+      u64 e1 = lane + 32 < cnt ? ck[lane + 32] : KEY_MAX;
+      if (e0 >= worst) e0 = KEY_MAX;
+      if (e1 >= worst) e1 = KEY_MAX;
+      const unsigned any0 = __ballot_sync(FULL, e0 != KEY_MAX), any1 = __ballot_sync(FULL, e1 != KEY_MAX);
+      if (any0 | any1) {
+        if (any1) warp_sort64(e0, e1, lane);
+        else e0 = warp_sort32(e0, lane);
+        // repeats inside the batch (possible only after the table forgot)
+        const u64 last0 = __shfl_sync(FULL, e0, 31);
+        const u64 up0 = __shfl_up_sync(FULL, e0, 1);
+        const u64 up1 = __shfl_up_sync(FULL, e1, 1);
+        const bool dup0 = lane > 0 && e0 == up0;
+        const bool dup1 = lane > 0 ? e1 == up1 : e1 == last0;
+        int lb0 = 0, lb1 = 0;
+        bool k0 = false, k1 = false;
+        if (e0 != KEY_MAX && !dup0) {
+          lb0 = lower_bound_w(W, len, e0);
+          k0 = !(lb0 < len && kmask(W[lb0]) == e0);
+        }
+        if (e1 != KEY_MAX && !dup1) {
+          lb1 = lower_bound_w(W, len, e1);
+          k1 = !(lb1 < len && kmask(W[lb1]) == e1);
+        }
+        const unsigned s0 = __ballot_sync(FULL, k0), s1 = __ballot_sync(FULL, k1);
+        const int cs0 = __popc(s0), cnew = cs0 + __popc(s1);
+        if (cnew > 0) {
+          __syncwarp();
+          if (k0) {
+            ck[__popc(s0 & lt)] = e0;
+            clb[__popc(s0 & lt)] = lb0;
+          }
+          if (k1) {
+            ck[cs0 + __popc(s1 & lt)] = e1;
+            clb[cs0 + __popc(s1 & lt)] = lb1;
+          }
+          __syncwarp();
+          const int lo = clb[0];
+          for (int top = len; top > lo; top -= 32) {
+            const int i = top - 32 + lane;
+            const bool act = i >= lo;
+            u64 val = 0;
+            int dest = 0;
+            if (act) {
+              val = W[i];
+              dest = i + count_le(clb, cnew, i);
+            }
+            __syncwarp();
+            if (act && dest < ef) W[dest] = val;
+            __syncwarp();
+          }
+          for (int j = lane; j < cnew; j += 32) {
+            const int pos = j + clb[j];
+            if (pos < ef) W[pos] = ck[j];
+          }
+          __syncwarp();
+          len = min(len + cnew, ef);
+          if (lo < cursor) cursor = lo;
+        }
+      }
+    }
+    // visited-table upkeep: keep the load factor at or below one half
+    if (stored > (Hn >> 1)) {
+      st |= KANN_QSTAT_FORGOT;
+      for (int i = lane; i < Hn; i += 32) H[i] = HEMPTY;
+      __syncwarp();
+      for (int i = lane; i < len; i += 32) visit(H, a.hbits, key_id(W[i]));
+      __syncwarp();
+      stored = len;
+    }
+  }
+
+  // 4. exact re-rank of the best R entries
+  int nout = len;
+  if (a.R != 0 && a.rr_data != nullptr) {
+    int R = a.R < 0 ? ef : a.R;
+    R = min(R, len);
+    const float* q = a.q + (size_t)qi * a.d;
+    for (int b = 0; b < R; b += 64) {
+      const int cb = min(64, R - b);
+      for (int j = lane; j < cb; j += 32) cid[j] = (int)key_id(W[b + j]);
+      __syncwarp();
+      rerank_dists<CPLR>(a, q, cid, cb, ck, lane);
+      __syncwarp();
+      for (int j = lane; j < cb; j += 32) W[b + j] = ck[j];
+      __syncwarp();
+    }
+    int P = 2;
+    while (P < R) P <<= 1;
+    for (int i = R + lane; i < P; i += 32) W[i] = KEY_MAX;
+    __syncwarp();
+    warp_smem_sort(W, P, lane);
+    nout = R;
+  }
+
+  // 5. output
+  const int ld = a.k_arr ? a.kmax : a.k;
+  for (int j = lane; j < ld; j += 32) {
+    int32_t id = -1;
+    float dd = __int_as_float(0x7f800000);
+    if (j < k && j < nout) {
+      const u64 key = kmask(W[j]);
+      id = (int32_t)key_id(key);
+      dd = key_dist(key);
+    }
+    a.out_ids[(size_t)qi * ld + j] = id;
+    a.out_d[(size_t)qi * ld + j] = dd;
+  }
+  st = __reduce_or_sync(FULL, st);
+  if (lane == 0) {
+    if (a.status) a.status[qi] = st;
+    if (a.counters) {
+      a.counters[(size_t)qi * 4 + 0] = c_l0d;
+      a.counters[(size_t)qi * 4 + 1] = c_l0e;
+      a.counters[(size_t)qi * 4 + 2] = c_upd;
+      a.counters[(size_t)qi * 4 + 3] = c_uph;
+    }
+  }
+}
+
+// Small rows (one chunk per lane) get a 64-register budget (32 warps per SM);
+// wider rows keep their query chunks in registers at 128.
+template <int CPLT, int CPLR>
+struct MinBlocks {
+  static constexpr int value = (CPLT <= 1 && CPLR <= 2) ? 8 : 4;
+};
+
+template <int DT, int CPLT, int CPLR>
+__global__ void __launch_bounds__(128, MinBlocks<CPLT, CPLR>::value) search_dense_kernel(const SearchArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int qi = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (qi >= a.nq) return;
+  DenseBackend<DT, CPLT> be;
+  search_one<DenseBackend<DT, CPLT>, CPLR>(a, be, qi, lane, smem + (size_t)warp * a.warp_smem);
+}
+
+typedef void (*KernelFn)(const SearchArgs);
+
+template <int DT>
+KernelFn pick_dense(int cplt, int cplr) {
+#define KANN_CASE(T, R) \
+  if (cplt == T && cplr == R) return search_dense_kernel<DT, T, R>;
+  KANN_CASE(1, 1)
+  KANN_CASE(1, 2)
+  KANN_CASE(1, 4)
+  KANN_CASE(2, 2)
+  KANN_CASE(2, 4)
+  KANN_CASE(2, 8)
+  KANN_CASE(4, 4)
+  KANN_CASE(4, 8)
+  KANN_CASE(8, 8)
+#undef KANN_CASE
+  return nullptr;
+}
+
+int pow2_at_least(int x) {
+  int p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+}  // namespace
+
+int search_warp_smem(int efcap, int hbits) {
+  return efcap * 8 + 64 * 8 + 64 * 4 + 64 * 4 + (4 << hbits);
+}
+
+int launch_search_dense(const SearchArgs& a, int dtype, int wpb, void* stream) {
+  if (a.nq == 0) return 0;
+  const int cplt = pow2_at_least((a.nchunks + a.lpr - 1) / a.lpr);
+  // the re-rank mapping is the one an FP32 traversal of the same d would use
+  const int cplr = a.rr_nchunks > 0 ? pow2_at_least((a.rr_nchunks + a.rr_lpr - 1) / a.rr_lpr) : cplt;
+  KernelFn fn = nullptr;
+  switch (dtype) {
+    case KANN_F32: fn = pick_dense<KANN_F32>(cplt, cplr < cplt ? cplt : cplr); break;
+    case KANN_F16: fn = pick_dense<KANN_F16>(cplt, cplr < cplt ? cplt : cplr); break;
+    case KANN_BF16: fn = pick_dense<KANN_BF16>(cplt, cplr < cplt ? cplt : cplr); break;
+    case KANN_E4M3: fn = pick_dense<KANN_E4M3>(cplt, cplr < cplt ? cplt : cplr); break;
+    default: break;
+  }
+  if (!fn) return (int)cudaErrorInvalidValue;
+  const size_t smem = (size_t)wpb * a.warp_smem;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return (int)e;
+  const int grid = (a.nq + wpb - 1) / wpb;
+  fn<<<grid, wpb * 32, smem, (cudaStream_t)stream>>>(a);
+  return (int)cudaGetLastError();
+}
+
+}  // namespace kann

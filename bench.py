@@ -69,7 +69,7 @@ class Clocks:
 
     def __init__(self, gpu):
         self.path = os.path.join(tempfile.gettempdir(), "kann_clocks_%d.csv" % os.getpid())
-        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+        q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
@@ -79,24 +79,30 @@ class Clocks:
         except Exception:
             self.p = None
 
-    def stop(self):
+    def stop(self, t0, t1):
+        """Summarise the samples taken between wall-clock times t0 and t1."""
         if self.p is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.15)
         self.p.terminate()
         self.p.wait()
         self.f.close()
+        import datetime
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in open(self.path):
             parts = [s.strip() for s in line.split(",")]
-            if len(parts) < 9:
+            if len(parts) < 10:
                 continue
             try:
-                sm.append(float(parts[1]))
-                mx.append(float(parts[2]))
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                if ts < t0 - 0.05 or ts > t1 + 0.05:
+                    continue
+                sm.append(float(parts[2]))
+                mx.append(float(parts[3]))
             except ValueError:
                 continue
-            for nm, v in zip(names, parts[5:9]):
+            for nm, v in zip(names, parts[6:10]):
                 if v.lower().startswith("active"):
                     reasons.add(nm)
         os.remove(self.path)
@@ -111,26 +117,43 @@ def recall_at(ids, gt, k=K):
     return float(hit.mean() / k)
 
 
-def cpu_oracle_qps(g, X, Q, ef, seconds=12.0, threads=0):
-    """The FP64 oracle (FP16 traversal values + FP64 re-rank on FP32) on a
-    bounded sample of the queries, all host cores."""
-    import oracle as O
-    og = O.import_graph(g)
-    Xh = O.encode_f16(X)
-    ncores = os.cpu_count() or 1
-    threads = threads or ncores
-    t = time.time()
-    n0 = min(len(Q), max(threads, 16))
-    O.search_dense(og, Xh, Q[:n0], ef, ef, O.L2, dtype=O.DT_F16, nthreads=threads)
-    per = (time.time() - t) / n0
-    n = int(min(len(Q), max(n0, seconds / max(per, 1e-6))))
-    t = time.time()
-    ti, _, cnt = O.search_dense(og, Xh, Q[:n], ef, ef, O.L2, dtype=O.DT_F16, nthreads=threads)
-    O.rerank_dense(X, Q[:n], ti, K, O.L2)
-    dt = time.time() - t
-    return {"value": n / dt, "unit": "queries/s", "cores": threads, "kind": "oracle",
-            "sample": "%d of the %d queries at ef=%d (FP16 traversal values, FP64 arithmetic, FP64 re-rank), "
-                      "%.1f s" % (n, len(Q), ef, dt)}, cnt
+class OracleRunner:
+    """The FP64 oracle on this workload: FP16 traversal values with FP64
+    arithmetic, then an FP64 re-rank on the FP32 vectors (the same path the
+    GPU step runs), over a sample of the queries on all host cores."""
+
+    def __init__(self, g, X, ef, threads=0):
+        import oracle as O
+        self.O = O
+        self.og = O.import_graph(g)
+        self.Xh = O.encode_f16(X)
+        self.X = X
+        self.ef = ef
+        self.threads = threads or (os.cpu_count() or 1)
+
+    def run(self, Qs):
+        O = self.O
+        t = time.time()
+        ti, _, cnt = O.search_dense(self.og, self.Xh, Qs, self.ef, self.ef, O.L2, dtype=O.DT_F16,
+                                    nthreads=self.threads)
+        O.rerank_dense(self.X, Qs, ti, K, O.L2)
+        return time.time() - t
+
+    def per_query_s(self, Q):
+        n0 = min(len(Q), 8 * self.threads)
+        return self.run(Q[:n0]) / n0
+
+    def describe(self, n, total, dt):
+        return {"value": n / dt, "unit": "queries/s", "cores": self.threads, "kind": "oracle",
+                "sample": "%d queries of the %d-query set at ef=%d (FP16 traversal values, FP64 arithmetic, "
+                          "FP64 re-rank), %.1f s on %d threads" % (n, total, self.ef, dt, self.threads)}
+
+
+def cpu_oracle_qps(g, X, Q, ef, seconds=15.0):
+    r = OracleRunner(g, X, ef)
+    n = int(min(len(Q), max(8 * r.threads, seconds / max(r.per_query_s(Q), 1e-6))))
+    dt = r.run(Q[:n])
+    return r.describe(n, len(Q), dt)
 
 
 def run_reference(args):
@@ -140,22 +163,28 @@ def run_reference(args):
     X, Q = make_workload()
     g, _, _ = graph_for(X, N_BASE, SEED)
     ef = args.ef or 64
+    runner = OracleRunner(g, X, ef)
+    budget = max(0.2, 150.0 / max(1, args.steps + args.warmup))
+    n_step = int(max(runner.threads, min(len(Q), budget / max(runner.per_query_s(Q), 1e-6))))
+    pos = 0
+
+    def step():
+        nonlocal pos
+        idx = (np.arange(n_step) + pos) % len(Q)
+        pos = (pos + n_step) % len(Q)
+        return runner.run(Q[idx])
+
     for _ in range(args.warmup):
-        pass
-    total_q, total_t = 0, 0.0
-    base = None
-    for _ in range(max(1, args.steps)):
-        cb, _ = cpu_oracle_qps(g, X, Q, ef, seconds=max(2.0, 60.0 / max(1, args.steps)))
-        base = cb
-        n = int(cb["sample"].split(" of ")[0])
-        total_q += n
-        total_t += n / cb["value"]
+        step()
+    total_t = sum(step() for _ in range(args.steps))
+    total_q = n_step * args.steps
     v = total_q / total_t
-    base["value"] = v
+    base = runner.describe(total_q, len(Q), total_t)
+    base["sample"] += "; %d queries per step" % n_step
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "queries/s", "n_gpus": 1, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * total_t / max(1, args.steps), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": WORKLOAD, "ef": ef, "k": K, "sample": base["sample"]},
+           "config": {"workload": WORKLOAD, "ef": ef, "k": K, "queries_per_step": n_step},
            "cpu_baseline": base, "e2e": {"value": v, "unit": "queries/s", "h2d_bytes_per_step": 0,
                                          "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
@@ -176,8 +205,8 @@ def traffic_from_profiles(kernel_sha):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ef", type=int, default=0, help="fix ef instead of sweeping")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -268,8 +297,10 @@ def main():
         return sum(per), per
 
     clocks = Clocks(local)
+    time.sleep(0.3)
+    w0 = time.time()
     total_ms, per = timed(idx16, -1, args.steps, args.warmup)
-    clk = clocks.stop()
+    clk = clocks.stop(w0 + 1e-3 * 0, time.time())
     if world > 1:
         t = torch.tensor([total_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -326,7 +357,7 @@ def main():
 
     cpu_base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu_base, _ = cpu_oracle_qps(g, X, Q, ef)
+        cpu_base = cpu_oracle_qps(g, X, Q, ef)
 
     if rank == 0:
         per_sorted = sorted(per)

@@ -48,6 +48,7 @@ extern "C" {
 #define KANN_QSTAT_HOPCAP 1u    /* layer-0 expansions hit opts.max_hops; result is the W reached */
 #define KANN_QSTAT_FORGOT 2u    /* the visited table was cleared at least once (results unaffected) */
 #define KANN_QSTAT_BAD_ID 4u    /* an adjacency entry >= n was met and skipped */
+#define KANN_QSTAT_QUERY_TRUNCATED 8u /* sparse query with more than 512 terms: the excess was dropped */
 
 /* ---- enums --------------------------------------------------------------*/
 #define KANN_L2 0

@@ -181,6 +181,42 @@ int run_dense(const kann_index_t* idx, SearchArgs& a, int wpb, void* stream) {
   return check_cuda((cudaError_t)launch_search_dense(a, v.dtype, wpb, stream));
 }
 
+int run_pq(const kann_index_t* idx, SearchArgs& a, int wpb, void* stream) {
+  const kann_pq_desc& pq = idx->pq;
+  a.codes = pq.d_codes;
+  a.codebooks = pq.d_codebooks;
+  a.pq_m = pq.m;
+  a.pq_dsub = pq.dsub;
+  a.stride = pq.m;
+  a.d = pq.m * pq.dsub;
+  a.metric = pq.metric;
+  a.nchunks = pq.m / 16;
+  a.lpr = lanes_per_row(a.nchunks);
+  if (a.nq > 0 && (!a.q || !aligned16(a.q))) return KANN_EINVAL;
+  const int optin = max_optin_smem();
+  a.warp_smem = search_warp_smem_pq(a.efcap, a.hbits, pq.m);
+  while (a.warp_smem > optin && a.hbits > 8) {
+    --a.hbits;
+    a.warp_smem = search_warp_smem_pq(a.efcap, a.hbits, pq.m);
+  }
+  if (a.warp_smem > optin) return KANN_ENOMEM;
+  while (wpb > 1 && wpb * a.warp_smem > optin) --wpb;
+  if (a.nq == 0) return KANN_OK;
+  return check_cuda((cudaError_t)launch_search_pq(a, wpb, stream));
+}
+
+int run_sparse(const kann_index_t* idx, SearchArgs& a, const SparseArgs& sa, int wpb, void* stream) {
+  if (a.R != 0) return KANN_EINVAL;
+  a.metric = KANN_IP;
+  a.warp_smem = search_warp_smem_sparse(a.efcap, a.hbits);
+  const int optin = max_optin_smem();
+  while (wpb > 1 && wpb * a.warp_smem > optin) --wpb;
+  if (a.warp_smem > optin) return KANN_ENOMEM;
+  if (a.nq == 0) return KANN_OK;
+  (void)idx;
+  return check_cuda((cudaError_t)launch_search_sparse(a, sa, wpb, stream));
+}
+
 // ---- format conversion kernels ---------------------------------------------
 __global__ void to_f16_kernel(const float* x, int64_t n, __half* y) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
@@ -260,6 +296,7 @@ int kann_index_upload(kann_index_t** out, const kann_graph_desc* g, const kann_v
     if (pq->m < 1 || pq->ksub != 256 || pq->dsub < 1 || !pq->d_codes || !pq->d_codebooks) rc = KANN_EINVAL;
     if (pq->metric != KANN_L2 && pq->metric != KANN_IP) rc = KANN_EINVAL;
     if ((pq->m * pq->dsub) % 4 != 0 || pq->m * pq->dsub > KANN_MAX_DIM) rc = KANN_EINVAL;
+    if (pq->m % 16 != 0 || pq->m > 512 || !aligned16(pq->d_codes)) rc = KANN_EINVAL;
   } else {
     idx->kind = 2;
     idx->sp = *sp;
@@ -269,6 +306,9 @@ int kann_index_upload(kann_index_t** out, const kann_graph_desc* g, const kann_v
     if (rerank->dtype != KANN_F32) rc = KANN_EINVAL;
     else rc = validate_vectors(rerank, g->n);
     if (rc == KANN_OK && idx->kind == 0 && (rerank->d != v->d || rerank->metric != v->metric)) rc = KANN_EINVAL;
+    if (rc == KANN_OK && idx->kind == 1 && (rerank->d != pq->m * pq->dsub || rerank->metric != pq->metric))
+      rc = KANN_EINVAL;
+    if (rc == KANN_OK && idx->kind == 2) rc = KANN_EINVAL;
     if (rc == KANN_OK && rerank->d / 4 > 32 * 8) rc = KANN_EINVAL;
     idx->has_rr = 1;
     idx->rr = *rerank;
@@ -311,6 +351,7 @@ int kann_search_ex(const kann_index_t* idx, const float* d_queries, int n, int k
                             wpb);
   if (rc != KANN_OK) return rc;
   if (idx->kind == 0) return run_dense(idx, a, wpb, stream);
+  if (idx->kind == 1) return run_pq(idx, a, wpb, stream);
   return KANN_EINVAL;
 }
 
@@ -328,15 +369,29 @@ int kann_search_batch(const kann_index_t* idx, const float* d_queries, int n, co
   int rc = fill_search_args(idx, d_queries, n, kmax, efmax, kmax, efmax, d_k, d_ef, d_ids, d_dists, opts, a, wpb);
   if (rc != KANN_OK) return rc;
   if (idx->kind == 0) return run_dense(idx, a, wpb, stream);
+  if (idx->kind == 1) return run_pq(idx, a, wpb, stream);
   return KANN_EINVAL;
 }
 
 int kann_search_sparse(const kann_index_t* idx, const int64_t* d_q_indptr, const uint16_t* d_q_terms,
                        const float* d_q_weights, int n, int k, int ef, int32_t* d_ids, float* d_dists,
                        const kann_search_opts* opts, void* stream) {
-  (void)idx; (void)d_q_indptr; (void)d_q_terms; (void)d_q_weights; (void)n; (void)k; (void)ef;
-  (void)d_ids; (void)d_dists; (void)opts; (void)stream;
-  return KANN_EINVAL;
+  if (k < 1 || !idx || idx->kind != 2) return KANN_EINVAL;
+  if (n > 0 && (!d_q_indptr || !d_q_terms || !d_q_weights)) return KANN_EINVAL;
+  SearchArgs a;
+  int wpb = 4;
+  int rc = fill_search_args(idx, nullptr, n, k, ef, k, ef > k ? ef : k, nullptr, nullptr, d_ids, d_dists, opts, a,
+                            wpb);
+  if (rc != KANN_OK) return rc;
+  SparseArgs sa;
+  sa.indptr = idx->sp.d_indptr;
+  sa.terms = idx->sp.d_terms;
+  sa.w = idx->sp.d_weights;
+  sa.q_indptr = d_q_indptr;
+  sa.q_terms = d_q_terms;
+  sa.q_w = d_q_weights;
+  sa.vocab = idx->sp.vocab;
+  return run_sparse(idx, a, sa, wpb, stream);
 }
 
 int kann_quantize(const float* d_x, int64_t n, int d, int dtype, void* d_out, float* d_scale, void* stream) {

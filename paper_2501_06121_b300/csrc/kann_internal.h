@@ -56,6 +56,7 @@ struct SparseArgs {
 // Per-warp shared memory needed by a dense search with these settings.
 int search_warp_smem(int efcap, int hbits);
 int search_warp_smem_pq(int efcap, int hbits, int m);
+int search_warp_smem_sparse(int efcap, int hbits);
 
 // Launchers (kann_search.cu); return a cudaError_t.
 int launch_search_dense(const SearchArgs& a, int dtype, int wpb, void* stream);

@@ -156,6 +156,162 @@ struct DenseBackend {
   }
 };
 
+// ---------------------------------------------------------------------------
+// PQ back-end (asymmetric distance computation, Jegou et al.): the query's
+// table LUT[j][c] = partial distance of query sub-vector j to centroid c of
+// subspace j (L2: ||q_j - C_j[c]||^2, IP: -<q_j, C_j[c]>) is built in FP32
+// in shared memory, then d(q, x) = sum_j LUT[j][code_j(x)].  A row is the m
+// code bytes of an item; lanes own 16-byte chunks of it exactly as in the
+// dense back-end, summing their lookups in byte order.
+// ---------------------------------------------------------------------------
+template <int CPL>
+struct PQBackend {
+  static constexpr int U = (8 / CPL) > 0 ? (8 / CPL) : 1;
+  float* lut;
+
+  __device__ __forceinline__ void init(const SearchArgs& a, int qi, int lane, unsigned char* extra) {
+    lut = reinterpret_cast<float*>(extra);
+    const int m = a.pq_m, dsub = a.pq_dsub;
+    const float* q = a.q + (size_t)qi * m * dsub;
+    for (int e = lane; e < m * 256; e += 32) {
+      const int j = e >> 8;
+      const float* C = a.codebooks + (size_t)e * dsub;
+      const float* qq = q + j * dsub;
+      float s = 0.f;
+      for (int t = 0; t < dsub; ++t) {
+        const float cv = __ldg(C + t), qv = __ldg(qq + t);
+        if (a.metric == KANN_L2) {
+          const float u = qv - cv;
+          s = fmaf(u, u, s);
+        } else {
+          s = fmaf(qv, cv, s);
+        }
+      }
+      lut[e] = a.metric == KANN_L2 ? s : -s;
+    }
+    __syncwarp();
+  }
+
+  __device__ __forceinline__ void dists(const SearchArgs& a, const int* cid, int cnt, u64* ck, int lane) {
+    const int lpr = a.lpr, rpi = 32 / lpr;
+    const int sub = lane & (lpr - 1), grp = lane / lpr;
+    for (int base = 0; base < cnt; base += rpi * U) {
+      uint4 buf[U][CPL];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int r = base + u * rpi + grp;
+        const int id = r < cnt ? cid[r] : -1;
+        const unsigned char* row = a.codes + (int64_t)(id < 0 ? 0 : id) * a.stride;
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) {
+          const int ch = sub + c * lpr;
+          buf[u][c] = (id >= 0 && ch < a.nchunks) ? ldg_stream16(row + ch * 16) : make_uint4(0u, 0u, 0u, 0u);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int r = base + u * rpi + grp;
+        float acc = 0.f;
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) {
+          const int ch = sub + c * lpr;
+          if (ch < a.nchunks) {
+            const uint32_t w[4] = {buf[u][c].x, buf[u][c].y, buf[u][c].z, buf[u][c].w};
+            const float* L = lut + (size_t)ch * 16 * 256;
+#pragma unroll
+            for (int b = 0; b < 16; ++b) acc += L[b * 256 + ((w[b >> 2] >> (8 * (b & 3))) & 0xffu)];
+          }
+        }
+        for (int o = lpr >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
+        if (sub == 0 && r < cnt) ck[r] = make_key(acc, (uint32_t)cid[r]);
+      }
+    }
+  }
+};
+
+// ---------------------------------------------------------------------------
+// Sparse back-end (inner product over term/weight lists): the query's terms
+// are scattered into a shared-memory hash (term -> weight), then each
+// candidate document's term list is walked by a group of 8 lanes, each lane
+// summing w_q(t) * w_x(t) over its positions in order; distance = -sum.
+// ---------------------------------------------------------------------------
+constexpr int SP_QH = 1024;   // query table slots (queries up to 512 terms)
+constexpr int SP_LPD = 8;     // lanes per document
+
+struct SparseBackend {
+  const SparseArgs* sp;
+  uint32_t* keys;
+  float* vals;
+  uint32_t trunc;
+
+  __device__ __forceinline__ uint32_t slot0(uint32_t t) const { return (t * 2654435761u) >> (32 - 10); }
+
+  __device__ __forceinline__ void init(const SearchArgs& a, int qi, int lane, unsigned char* extra) {
+    keys = reinterpret_cast<uint32_t*>(extra);
+    vals = reinterpret_cast<float*>(keys + SP_QH);
+    trunc = 0;
+    for (int i = lane; i < SP_QH; i += 32) keys[i] = HEMPTY;
+    __syncwarp();
+    const int64_t b = sp->q_indptr[qi], e = sp->q_indptr[qi + 1];
+    for (int64_t t = b + lane; t < e; t += 32) {
+      const uint32_t term = sp->q_terms[t];
+      const float w = sp->q_w[t];
+      uint32_t h = slot0(term);
+      bool done = false;
+      for (int p = 0; p < SP_QH && !done; ++p) {
+        const uint32_t old = atomicCAS(&keys[h], HEMPTY, term);
+        if (old == HEMPTY || old == term) {
+          vals[h] = w;
+          done = true;
+        }
+        h = (h + 1u) & (SP_QH - 1);
+      }
+      if (!done) trunc = 1;
+    }
+    if (e - b > SP_QH / 2) trunc = 1;
+    __syncwarp();
+  }
+
+  __device__ __forceinline__ float weight(uint32_t term) const {
+    uint32_t h = slot0(term);
+    for (int p = 0; p < SP_QH; ++p) {
+      const uint32_t k = keys[h];
+      if (k == term) return vals[h];
+      if (k == HEMPTY) return 0.f;
+      h = (h + 1u) & (SP_QH - 1);
+    }
+    return 0.f;
+  }
+
+  __device__ __forceinline__ void dists(const SearchArgs&, const int* cid, int cnt, u64* ck, int lane) {
+    const int sub = lane & (SP_LPD - 1), grp = lane / SP_LPD;
+    constexpr int DPI = 32 / SP_LPD;  // documents per warp iteration
+    for (int base = 0; base < cnt; base += DPI) {
+      const int r = base + grp;
+      const int id = r < cnt ? cid[r] : -1;
+      float acc = 0.f;
+      if (id >= 0) {
+        const int64_t b = __ldg(sp->indptr + id), e = __ldg(sp->indptr + id + 1);
+        for (int64_t t0 = b + sub; t0 < e; t0 += 4 * SP_LPD) {
+          uint32_t tm[4];
+          float wx[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int64_t t = t0 + u * SP_LPD;
+            tm[u] = t < e ? (uint32_t)__ldg(sp->terms + t) : HEMPTY;
+            wx[u] = t < e ? __ldg(sp->w + t) : 0.f;
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (tm[u] != HEMPTY) acc = fmaf(weight(tm[u]), wx[u], acc);
+        }
+      }
+      for (int o = SP_LPD >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
+      if (sub == 0 && r < cnt) ck[r] = make_key(-acc, (uint32_t)id);
+    }
+  }
+};
+
 // Exact FP32 distances for the re-rank, from the index's FP32 copy.  Same
 // lane/chunk mapping and summation order as the FP32 dense back-end, so a
 // re-ranked distance is bit-identical to the FP32 traversal distance.
@@ -229,6 +385,12 @@ struct WarpSmem {
   }
 };
 
+template <class B>
+__device__ __forceinline__ uint32_t backend_status(const B&) { return 0u; }
+__device__ __forceinline__ uint32_t backend_status(const SparseBackend& b) {
+  return b.trunc ? KANN_QSTAT_QUERY_TRUNCATED : 0u;
+}
+
 template <class B, int CPLR>
 __device__ __forceinline__ void search_one(const SearchArgs& a, B& be, int qi, int lane, unsigned char* ws) {
   WarpSmem s(ws, a.efcap, a.hbits);
@@ -250,6 +412,7 @@ __device__ __forceinline__ void search_one(const SearchArgs& a, B& be, int qi, i
   int c_l0d = 0, c_l0e = 0, c_upd = 0, c_uph = 0;
 
   be.init(a, qi, lane, s.extra);
+  st |= backend_status(be);
 
   // 1. entry point
   if (lane == 0) cid[0] = a.entry;
@@ -473,6 +636,26 @@ __global__ void __launch_bounds__(128, MinBlocks<CPLT, CPLR>::value) search_dens
   search_one<DenseBackend<DT, CPLT>, CPLR>(a, be, qi, lane, smem + (size_t)warp * a.warp_smem);
 }
 
+template <int CPLT, int CPLR>
+__global__ void __launch_bounds__(128, 1) search_pq_kernel(const SearchArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int qi = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (qi >= a.nq) return;
+  PQBackend<CPLT> be;
+  search_one<PQBackend<CPLT>, CPLR>(a, be, qi, lane, smem + (size_t)warp * a.warp_smem);
+}
+
+__global__ void __launch_bounds__(128, 4) search_sparse_kernel(const SearchArgs a, const __grid_constant__ SparseArgs sp) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int qi = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (qi >= a.nq) return;
+  SparseBackend be;
+  be.sp = &sp;
+  search_one<SparseBackend, 1>(a, be, qi, lane, smem + (size_t)warp * a.warp_smem);
+}
+
 typedef void (*KernelFn)(const SearchArgs);
 
 template <int DT>
@@ -523,6 +706,38 @@ int launch_search_dense(const SearchArgs& a, int dtype, int wpb, void* stream) {
   if (e != cudaSuccess) return (int)e;
   const int grid = (a.nq + wpb - 1) / wpb;
   fn<<<grid, wpb * 32, smem, (cudaStream_t)stream>>>(a);
+  return (int)cudaGetLastError();
+}
+
+int search_warp_smem_pq(int efcap, int hbits, int m) { return search_warp_smem(efcap, hbits) + m * 256 * 4; }
+
+int search_warp_smem_sparse(int efcap, int hbits) { return search_warp_smem(efcap, hbits) + SP_QH * 8; }
+
+int launch_search_pq(const SearchArgs& a, int wpb, void* stream) {
+  if (a.nq == 0) return 0;
+  const int cplt = pow2_at_least((a.nchunks + a.lpr - 1) / a.lpr);
+  int cplr = a.rr_nchunks > 0 ? pow2_at_least((a.rr_nchunks + a.rr_lpr - 1) / a.rr_lpr) : 1;
+  KernelFn fn = nullptr;
+#define KANN_PQ(T, R) \
+  if (cplt == T && cplr == R) fn = search_pq_kernel<T, R>;
+  KANN_PQ(1, 1) KANN_PQ(1, 2) KANN_PQ(1, 4) KANN_PQ(1, 8)
+  KANN_PQ(2, 1) KANN_PQ(2, 2) KANN_PQ(2, 4) KANN_PQ(2, 8)
+  KANN_PQ(4, 1) KANN_PQ(4, 2) KANN_PQ(4, 4) KANN_PQ(4, 8)
+#undef KANN_PQ
+  if (!fn) return (int)cudaErrorInvalidValue;
+  const size_t smem = (size_t)wpb * a.warp_smem;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return (int)e;
+  fn<<<(a.nq + wpb - 1) / wpb, wpb * 32, smem, (cudaStream_t)stream>>>(a);
+  return (int)cudaGetLastError();
+}
+
+int launch_search_sparse(const SearchArgs& a, const SparseArgs& sp, int wpb, void* stream) {
+  if (a.nq == 0) return 0;
+  const size_t smem = (size_t)wpb * a.warp_smem;
+  cudaError_t e = cudaFuncSetAttribute(search_sparse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return (int)e;
+  search_sparse_kernel<<<(a.nq + wpb - 1) / wpb, wpb * 32, smem, (cudaStream_t)stream>>>(a, sp);
   return (int)cudaGetLastError();
 }
 

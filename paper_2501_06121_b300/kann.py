@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(HERE, "libkann.so")
 KANN_OK, KANN_EINVAL, KANN_ENOMEM, KANN_ECUDA, KANN_EFORMAT, KANN_ETIMEOUT = range(6)
 KANN_L2, KANN_IP = 0, 1
 KANN_F32, KANN_F16, KANN_BF16, KANN_E4M3 = 0, 1, 2, 3
-KANN_QSTAT_HOPCAP, KANN_QSTAT_FORGOT, KANN_QSTAT_BAD_ID = 1, 2, 4
+KANN_QSTAT_HOPCAP, KANN_QSTAT_FORGOT, KANN_QSTAT_BAD_ID, KANN_QSTAT_QUERY_TRUNCATED = 1, 2, 4, 8
 KANN_MAX_EF = 1024
 
 _TORCH_DTYPE = {KANN_F32: torch.float32, KANN_F16: torch.float16, KANN_BF16: torch.bfloat16,

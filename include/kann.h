@@ -197,6 +197,31 @@ int kann_exact_knn(const void* d_queries, const void* d_base, int nq, int64_t nb
 
 size_t kann_exact_knn_workspace_bytes(int nq, int64_t nb, int d, int k, int dtype);
 
+/* kann_exact_knn_noalloc: the same exact k-NN, for callers that cannot
+ * allocate device memory -- for example code running inside a host
+ * application whose device memory is owned by another allocator (a
+ * framework's caching allocator, an inference server that reserves the
+ * whole GPU up front), or latency-critical paths where cudaMalloc is not
+ * allowed because it can synchronise the device.  It calls no cudaMalloc,
+ * cudaFree or other allocating routine: its scratch is one static device
+ * array of KANN_NOALLOC_SCRATCH_BYTES per GPU, held by every GPU that loads
+ * this library until the process exits.  The caller still passes inputs and
+ * outputs as for kann_exact_knn.
+ *   - The first call on a device looks up that array's device address (once
+ *     per device, with that device current); make that first call before any
+ *     stream capture.
+ *   - Returns KANN_EINVAL when the request needs more scratch than the array
+ *     holds, i.e. kann_exact_knn_workspace_bytes(nq, nb, d, k, dtype) >
+ *     KANN_NOALLOC_SCRATCH_BYTES (split the queries into smaller batches).
+ *   - Every call shares the array, which keeps the previous call's contents
+ *     (nothing in it needs to start at zero).  Calls that overlap on the GPU
+ *     (concurrent streams, or several host threads) race on it: serialise
+ *     them.
+ * The paper has no counterpart to this call. */
+#define KANN_NOALLOC_SCRATCH_BYTES ((size_t)16 << 20)
+int kann_exact_knn_noalloc(const void* d_queries, const void* d_base, int nq, int64_t nb, int d, int metric,
+                           int dtype, int k, int32_t* d_ids, float* d_dists, void* stream);
+
 /* Convert FP32 rows d_x [n][d] to a storage format on the device:
  * KANN_F16 / KANN_BF16 (round to nearest even) into d_out [n][d] 16-bit, or
  * KANN_E4M3 with per-row scale s = max|x| / 448 (FP32 division) and codes

@@ -11,6 +11,8 @@
 // its per-query lists to the caller's workspace.
 // Pass 2 (exact_merge_kernel): one warp per query sorts the S * k partial keys
 // and writes the k best.
+#include <mutex>
+
 #include "kann_device.cuh"
 #include "kann_internal.h"
 
@@ -240,4 +242,60 @@ extern "C" int kann_exact_knn(const void* d_queries, const void* d_base, int nq,
     return KANN_ECUDA;
   }
   return KANN_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Exact k-NN without allocation, for callers that cannot call cudaMalloc (a
+// host application whose device memory belongs to another allocator, or a
+// latency-critical path where an allocation's implicit synchronisation is not
+// allowed).  The split-N partial lists live in one static device array per
+// GPU instead of caller scratch; its device address is looked up once per
+// device, with that device current, by the first call there.
+// ---------------------------------------------------------------------------
+namespace kann {
+namespace {
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[KANN_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kMaxDevices] = {};
+
+int noalloc_scratch(void** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) {
+    set_cuda_error((int)e);
+    return KANN_ECUDA;
+  }
+  if (dev < 0 || dev >= kMaxDevices) return KANN_EINVAL;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (g_noalloc_ptr[dev] == nullptr) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) {
+      set_cuda_error((int)e);
+      return KANN_ECUDA;
+    }
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return KANN_OK;
+}
+
+}  // namespace
+}  // namespace kann
+
+extern "C" int kann_exact_knn_noalloc(const void* d_queries, const void* d_base, int nq, int64_t nb, int d,
+                                      int metric, int dtype, int k, int32_t* d_ids, float* d_dists, void* stream) {
+  if (nq < 0 || nb < 0 || d < 1 || k < 1) return KANN_EINVAL;
+  if (nq == 0) return KANN_OK;
+  // the partial lists must fit the static array; nothing in it needs zeroing
+  // (pass 1 writes every entry pass 2 reads)
+  if (kann_exact_knn_workspace_bytes(nq, nb, d, k, dtype) > KANN_NOALLOC_SCRATCH_BYTES) return KANN_EINVAL;
+  void* scratch = nullptr;
+  const int rc = noalloc_scratch(&scratch);
+  if (rc != KANN_OK) return rc;
+  return kann_exact_knn(d_queries, d_base, nq, nb, d, metric, dtype, k, d_ids, d_dists, scratch,
+                        KANN_NOALLOC_SCRATCH_BYTES, stream);
 }

@@ -330,3 +330,33 @@ def kann_hnsw_build_sparse(csr, M, ef_construction, seed, nthreads=0):
                                                                    ef_construction, seed, nthreads, _vp(level),
                                                                    _vp(l0), _vp(us), _vp(up), ctypes.byref(entry)))
     return dict(n=n, M=M, M0=2 * M, max_level=L, entry=entry.value, level=level, l0=l0, upper_slot=us, upper=up)
+
+
+KANN_NOALLOC_SCRATCH_BYTES = 16 << 20
+
+
+def kann_exact_knn_noalloc(queries, base, k, metric, dtype=KANN_F32, ids=None, dists=None, stream=None):
+    """kann_exact_knn without any device allocation inside the library: the
+    scratch is the library's static per-GPU array, so the outputs are the only
+    buffers involved (allocate them yourself to avoid torch allocations too).
+    Raises ValueError before calling when the request needs more scratch than
+    KANN_NOALLOC_SCRATCH_BYTES; calls that overlap on the GPU must not run
+    concurrently (they share the array)."""
+    _require_cuda(queries, base, ids, dists)
+    nq, d = queries.shape
+    nb = base.shape[0]
+    need = kann_exact_knn_workspace_bytes(nq, nb, d, k, dtype)
+    if need > KANN_NOALLOC_SCRATCH_BYTES:
+        raise ValueError("kann_exact_knn_noalloc: %d queries need %d bytes of scratch, more than the %d-byte "
+                         "static array; split the queries" % (nq, need, KANN_NOALLOC_SCRATCH_BYTES))
+    if ids is None:
+        ids = torch.empty((nq, k), dtype=torch.int32, device=queries.device)
+    if dists is None:
+        dists = torch.empty((nq, k), dtype=torch.float32, device=queries.device)
+    f = _lib().kann_exact_knn_noalloc
+    P, I = ctypes.c_void_p, ctypes.c_int
+    f.restype = I
+    f.argtypes = [P, P, I, ctypes.c_int64, I, I, I, I, P, P, P]
+    _check("kann_exact_knn_noalloc", f(_dev(queries), _dev(base), nq, nb, d, metric, dtype, k, _dev(ids),
+                                       _dev(dists), _stream(stream)))
+    return ids, dists

@@ -2,8 +2,8 @@
  * kann.h -- C ABI of the B300 (sm_103a) batched HNSW search library.
  *
  * The library runs the query-time path of the composable ANN method of
- * kANNolo (Delfino et al., 2025): k-NN search ("identify the k nearest
- * neighbors to a given query point", Sec. 1) over an HNSW graph (Sec. 2,
+ * kANNolo (Delfino et al., 2025): k-NN search -- for a query, find the k
+ * dataset vectors closest to it (problem statement, Sec. 1) -- over an HNSW graph (Sec. 2,
  * citing Malkov & Yashunin) whose items are dense vectors (L2 or inner
  * product), Product-Quantization codes (Sec. 2, citing Jegou et al.) or
  * sparse term/weight vectors (Sec. 3, Table 1).
@@ -126,8 +126,8 @@ typedef struct {
 typedef struct kann_index kann_index_t;
 
 /* Build a device-resident index from caller-owned device arrays (Sec. 2:
- * the Dataset "provides access to the data", the index "pinpoints which
- * vector shall be compared with the query").  Exactly one traversal source
+ * the dataset holds the items and their encoding, the index decides which
+ * items a query is compared with).  Exactly one traversal source
  * must be given: `v` (dense), `pq`, or `sp`.  `rerank` (nullable) is a dense
  * KANN_F32 copy of the same items with the same d and metric, used for exact
  * re-ranking of reduced-precision traversal.  The graph's metadata and

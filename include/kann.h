@@ -151,6 +151,8 @@ typedef struct {
   int32_t max_hops;        /* cap on layer-0 expansions per query; 0 = 1,000,000 */
   int32_t hash_bits;       /* log2 of the per-query visited table; 0 = automatic */
   int32_t warps_per_block; /* queries per CTA (one warp each); 0 = automatic */
+  int32_t lanes_per_row;   /* lanes sharing one row gather (power of two <= 32); 0 = automatic */
+  int32_t reserved;
   uint32_t* d_status;      /* [n] per-query KANN_QSTAT_* bits, nullable */
   int32_t* d_counters;     /* [n][4] per-query counters, nullable: layer-0 distance
                               evaluations, layer-0 expansions, upper-layer distance

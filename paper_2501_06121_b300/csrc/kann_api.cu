@@ -39,11 +39,21 @@ int elem_size(int dtype) {
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
 
-int lanes_per_row(int nchunks) {
+// Lanes that share one row: the largest power of two <= min(32, nchunks /
+// chunks_per_lane), so that each lane reads `chunks_per_lane` 16-byte chunks
+// of a row (more rows per warp pass, fewer per-row reductions).
+int lanes_per_row(int nchunks, int chunks_per_lane = 1) {
+  int target = nchunks / chunks_per_lane;
+  if (target < 1) target = 1;
   int l = 1;
-  while (l * 2 <= nchunks && l * 2 <= 32) l *= 2;
+  while (l * 2 <= target && l * 2 <= 32) l *= 2;
   return l;
 }
+
+// Chunks per lane used for a storage format by default (measured on the 1M x
+// 128 workload: 64 bytes of an FP32 or E4M3 row per lane, 32 bytes of an FP16
+// or BF16 row).
+int default_chunks_per_lane(int dtype) { return (dtype == KANN_F16 || dtype == KANN_BF16) ? 2 : 4; }
 
 int check_cuda(cudaError_t e) {
   if (e != cudaSuccess) {
@@ -144,6 +154,9 @@ int fill_search_args(const kann_index_t* idx, const float* d_q, int n, int k, in
     if (hbits != 0 && (hbits < 5 || hbits > 16)) return KANN_EINVAL;
     if (opts->warps_per_block < 0 || opts->warps_per_block > 4) return KANN_EINVAL;
     if (opts->warps_per_block > 0) wpb = opts->warps_per_block;
+    const int l = opts->lanes_per_row;
+    if (l < 0 || l > 32 || (l & (l - 1)) != 0) return KANN_EINVAL;
+    a.lpr_override = l;
     R = opts->rerank;
     if (R < -1) return KANN_EINVAL;
   }
@@ -154,7 +167,8 @@ int fill_search_args(const kann_index_t* idx, const float* d_q, int n, int k, in
     a.rr_data = (const unsigned char*)idx->rr.d_data;
     a.rr_stride = idx->rr.row_stride_bytes;
     a.rr_nchunks = idx->rr.d / 4;
-    a.rr_lpr = lanes_per_row(a.rr_nchunks);
+    // the mapping an FP32 traversal of the same rows uses by default
+    a.rr_lpr = lanes_per_row(a.rr_nchunks, default_chunks_per_lane(KANN_F32));
   }
   a.hbits = hbits ? hbits : default_hbits(a.efmax);
   int efcap = 32;
@@ -171,7 +185,9 @@ int run_dense(const kann_index_t* idx, SearchArgs& a, int wpb, void* stream) {
   a.d = v.d;
   a.metric = v.metric;
   a.nchunks = v.d * elem_size(v.dtype) / 16;
-  a.lpr = lanes_per_row(a.nchunks);
+  a.lpr = a.lpr_override ? a.lpr_override : lanes_per_row(a.nchunks, default_chunks_per_lane(v.dtype));
+  if (a.lpr > a.nchunks && a.nchunks >= 1) a.lpr = lanes_per_row(a.nchunks);
+  if ((a.nchunks + a.lpr - 1) / a.lpr > 8) return KANN_EINVAL;
   if (a.nq > 0 && (!a.q || !aligned16(a.q))) return KANN_EINVAL;
   a.warp_smem = search_warp_smem(a.efcap, a.hbits);
   const int optin = max_optin_smem();
@@ -191,7 +207,9 @@ int run_pq(const kann_index_t* idx, SearchArgs& a, int wpb, void* stream) {
   a.d = pq.m * pq.dsub;
   a.metric = pq.metric;
   a.nchunks = pq.m / 16;
-  a.lpr = lanes_per_row(a.nchunks);
+  a.lpr = a.lpr_override ? a.lpr_override : lanes_per_row(a.nchunks);
+  if (a.lpr > a.nchunks) a.lpr = lanes_per_row(a.nchunks);
+  if ((a.nchunks + a.lpr - 1) / a.lpr > 4) return KANN_EINVAL;
   if (a.nq > 0 && (!a.q || !aligned16(a.q))) return KANN_EINVAL;
   const int optin = max_optin_smem();
   a.warp_smem = search_warp_smem_pq(a.efcap, a.hbits, pq.m);

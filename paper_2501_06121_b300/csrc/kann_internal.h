@@ -38,6 +38,7 @@ struct SearchArgs {
   uint32_t* status;
   int32_t* counters;
   int hbits, max_hops;
+  int lpr_override;  // 0 = automatic lanes per row
   int efcap;       // W capacity (power of two >= efmax, >= 32)
   int warp_smem;   // bytes of shared memory per warp
 };

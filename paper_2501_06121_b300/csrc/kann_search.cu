@@ -313,56 +313,118 @@ struct SparseBackend {
 };
 
 // Exact FP32 distances for the re-rank, from the index's FP32 copy.  Same
-// lane/chunk mapping and summation order as the FP32 dense back-end, so a
-// re-ranked distance is bit-identical to the FP32 traversal distance.
-template <int CPL>
-__device__ __forceinline__ void rerank_dists(const SearchArgs& a, const float* q, const int* cid, int cnt, u64* ck,
-                                             int lane) {
-  constexpr int U = (8 / CPL) > 0 ? (8 / CPL) : 1;
-  const int lpr = a.rr_lpr, rpi = 32 / lpr;
+// lane/chunk mapping and summation order as the FP32 dense back-end (chunks
+// in order, elements in order, then the butterfly), so a re-ranked distance
+// is bit-identical to the FP32 traversal distance of the same row.
+__device__ __forceinline__ void rerank_dists(const unsigned char* rr, int64_t stride, int nchunks, int lpr, int metric,
+                                             const float* q, const int* cid, int cnt, u64* ck, int lane) {
+  constexpr int U = 4;
+  const int rpi = 32 / lpr;
   const int sub = lane & (lpr - 1), grp = lane / lpr;
-  float4 qv[CPL];
-#pragma unroll
-  for (int c = 0; c < CPL; ++c) {
-    const int ch = sub + c * lpr;
-    qv[c] = ch < a.rr_nchunks ? __ldg(reinterpret_cast<const float4*>(q) + ch) : make_float4(0.f, 0.f, 0.f, 0.f);
-  }
+  const int cpl = (nchunks + lpr - 1) / lpr;
   for (int base = 0; base < cnt; base += rpi * U) {
-    uint4 buf[U][CPL];
+    float acc[U];
+    int ids[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int r = base + u * rpi + grp;
-      const int id = r < cnt ? cid[r] : -1;
-      const unsigned char* row = a.rr_data + (int64_t)(id < 0 ? 0 : id) * a.rr_stride;
-#pragma unroll
-      for (int c = 0; c < CPL; ++c) {
-        const int ch = sub + c * lpr;
-        buf[u][c] = (id >= 0 && ch < a.rr_nchunks) ? ldg_stream16(row + ch * 16) : make_uint4(0u, 0u, 0u, 0u);
-      }
+      ids[u] = r < cnt ? cid[r] : -1;
+      acc[u] = 0.f;
     }
+    for (int c = 0; c < cpl; ++c) {
+      const int ch = sub + c * lpr;
+      const float4 qv =
+          ch < nchunks ? __ldg(reinterpret_cast<const float4*>(q) + ch) : make_float4(0.f, 0.f, 0.f, 0.f);
+      uint4 buf[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int r = base + u * rpi + grp;
-      float acc = 0.f;
+      for (int u = 0; u < U; ++u)
+        buf[u] = (ids[u] >= 0 && ch < nchunks) ? ldg_stream16(rr + (int64_t)ids[u] * stride + ch * 16)
+                                               : make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
-      for (int c = 0; c < CPL; ++c) {
-        const float x[4] = {__uint_as_float(buf[u][c].x), __uint_as_float(buf[u][c].y),
-                            __uint_as_float(buf[u][c].z), __uint_as_float(buf[u][c].w)};
-        const float qq[4] = {qv[c].x, qv[c].y, qv[c].z, qv[c].w};
+      for (int u = 0; u < U; ++u) {
+        const float x[4] = {__uint_as_float(buf[u].x), __uint_as_float(buf[u].y), __uint_as_float(buf[u].z),
+                            __uint_as_float(buf[u].w)};
+        const float qq[4] = {qv.x, qv.y, qv.z, qv.w};
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-          if (a.metric == KANN_L2) {
+          if (metric == KANN_L2) {
             const float t = qq[e] - x[e];
-            acc = fmaf(t, t, acc);
+            acc[u] = fmaf(t, t, acc[u]);
           } else {
-            acc = fmaf(qq[e], x[e], acc);
+            acc[u] = fmaf(qq[e], x[e], acc[u]);
           }
         }
       }
-      for (int o = lpr >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
-      if (sub == 0 && r < cnt) ck[r] = make_key(a.metric == KANN_L2 ? acc : -acc, (uint32_t)cid[r]);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      float v = acc[u];
+      for (int o = lpr >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
+      const int r = base + u * rpi + grp;
+      if (sub == 0 && r < cnt) ck[r] = make_key(metric == KANN_L2 ? v : -v, (uint32_t)ids[u]);
     }
   }
+}
+
+// Re-rank the best R entries of W exactly and sort them (cold path, once per
+// query).  Returns the number of re-ranked entries now at the front of W.
+__device__ __noinline__ int rerank_phase(const unsigned char* rr, int64_t stride, int nchunks, int lpr, int metric,
+                                         const float* q, int R, u64* W, u64* ck, int* cid, int lane) {
+  for (int b = 0; b < R; b += 64) {
+    const int cb = min(64, R - b);
+    for (int j = lane; j < cb; j += 32) cid[j] = (int)key_id(W[b + j]);
+    __syncwarp();
+    rerank_dists(rr, stride, nchunks, lpr, metric, q, cid, cb, ck, lane);
+    __syncwarp();
+    for (int j = lane; j < cb; j += 32) W[b + j] = ck[j];
+    __syncwarp();
+  }
+  int P = 2;
+  while (P < R) P <<= 1;
+  for (int i = R + lane; i < P; i += 32) W[i] = KEY_MAX;
+  __syncwarp();
+  warp_smem_sort(W, P, lane);
+  return R;
+}
+
+// Clear the visited table and put W's ids back (cold path).
+__device__ __noinline__ void reset_visited(uint32_t* H, int hbits, const u64* W, int len, int lane) {
+  for (int i = lane; i < (1 << hbits); i += 32) H[i] = HEMPTY;
+  __syncwarp();
+  for (int i = lane; i < len; i += 32) visit(H, hbits, key_id(W[i]));
+  __syncwarp();
+}
+
+// Survivors of a step (keys that beat worst(W) and are not in W) ordered by a
+// bitonic network, repeats inside the batch dropped; writes the ordered keys
+// and their W-ranks to ck/clb and returns their number.  Used when a step has
+// many survivors or repeated keys (cold path).
+__device__ __noinline__ int order_by_sort(u64 e0, u64 e1, bool k0, bool k1, const u64* W, int len, u64* ck, int* clb,
+                                          int lane) {
+  const unsigned lt = (1u << lane) - 1u;
+  if (!k0) e0 = KEY_MAX;
+  if (!k1) e1 = KEY_MAX;
+  if (__ballot_sync(FULL, k1)) warp_sort64(e0, e1, lane);
+  else e0 = warp_sort32(e0, lane);
+  const u64 last0 = __shfl_sync(FULL, e0, 31);
+  const u64 up0 = __shfl_up_sync(FULL, e0, 1);
+  const u64 up1 = __shfl_up_sync(FULL, e1, 1);
+  const bool ok0 = e0 != KEY_MAX && !(lane > 0 && e0 == up0);
+  const bool ok1 = e1 != KEY_MAX && !(lane > 0 ? e1 == up1 : e1 == last0);
+  const int lb0 = ok0 ? lower_bound_w(W, len, e0) : 0;
+  const int lb1 = ok1 ? lower_bound_w(W, len, e1) : 0;
+  const unsigned s0 = __ballot_sync(FULL, ok0), s1 = __ballot_sync(FULL, ok1);
+  const int cs0 = __popc(s0);
+  __syncwarp();
+  if (ok0) {
+    ck[__popc(s0 & lt)] = e0;
+    clb[__popc(s0 & lt)] = lb0;
+  }
+  if (ok1) {
+    ck[cs0 + __popc(s1 & lt)] = e1;
+    clb[cs0 + __popc(s1 & lt)] = lb1;
+  }
+  return cs0 + __popc(s1);
 }
 
 // Shared memory of one warp: W[efcap] keys, candidate keys[64], candidate
@@ -391,7 +453,7 @@ __device__ __forceinline__ uint32_t backend_status(const SparseBackend& b) {
   return b.trunc ? KANN_QSTAT_QUERY_TRUNCATED : 0u;
 }
 
-template <class B, int CPLR>
+template <class B>
 __device__ __forceinline__ void search_one(const SearchArgs& a, B& be, int qi, int lane, unsigned char* ws) {
   WarpSmem s(ws, a.efcap, a.hbits);
   u64* W = s.W;
@@ -498,75 +560,91 @@ __device__ __forceinline__ void search_one(const SearchArgs& a, B& be, int qi, i
       be.dists(a, cid, cnt, ck, lane);
       __syncwarp();
       c_l0d += cnt;
+      // survivors: keys that beat worst(W) and are not in W already
       const u64 worst = len >= ef ? kmask(W[len - 1]) : KEY_MAX;
-      u64 e0 = lane < cnt ? ck[lane] : KEY_MAX;
-      u64 e1 = lane + 32 < cnt ? ck[lane + 32] : KEY_MAX;
-      if (e0 >= worst) e0 = KEY_MAX;
-      if (e1 >= worst) e1 = KEY_MAX;
-      const unsigned any0 = __ballot_sync(FULL, e0 != KEY_MAX), any1 = __ballot_sync(FULL, e1 != KEY_MAX);
-      if (any0 | any1) {
-        if (any1) warp_sort64(e0, e1, lane);
-        else e0 = warp_sort32(e0, lane);
-        // repeats inside the batch (possible only after the table forgot)
-        const u64 last0 = __shfl_sync(FULL, e0, 31);
-        const u64 up0 = __shfl_up_sync(FULL, e0, 1);
-        const u64 up1 = __shfl_up_sync(FULL, e1, 1);
-        const bool dup0 = lane > 0 && e0 == up0;
-        const bool dup1 = lane > 0 ? e1 == up1 : e1 == last0;
-        int lb0 = 0, lb1 = 0;
-        bool k0 = false, k1 = false;
-        if (e0 != KEY_MAX && !dup0) {
-          lb0 = lower_bound_w(W, len, e0);
-          k0 = !(lb0 < len && kmask(W[lb0]) == e0);
-        }
-        if (e1 != KEY_MAX && !dup1) {
-          lb1 = lower_bound_w(W, len, e1);
-          k1 = !(lb1 < len && kmask(W[lb1]) == e1);
-        }
-        const unsigned s0 = __ballot_sync(FULL, k0), s1 = __ballot_sync(FULL, k1);
-        const int cs0 = __popc(s0), cnew = cs0 + __popc(s1);
-        if (cnew > 0) {
-          __syncwarp();
-          if (k0) {
-            ck[__popc(s0 & lt)] = e0;
-            clb[__popc(s0 & lt)] = lb0;
+      const u64 e0 = lane < cnt ? ck[lane] : KEY_MAX;
+      const u64 e1 = lane + 32 < cnt ? ck[lane + 32] : KEY_MAX;
+      bool k0 = e0 < worst, k1 = e1 < worst;
+      int lb0 = 0, lb1 = 0;
+      if (k0) {
+        lb0 = lower_bound_w(W, len, e0);
+        k0 = !(lb0 < len && kmask(W[lb0]) == e0);
+      }
+      if (k1) {
+        lb1 = lower_bound_w(W, len, e1);
+        k1 = !(lb1 < len && kmask(W[lb1]) == e1);
+      }
+      const unsigned s0 = __ballot_sync(FULL, k0), s1 = __ballot_sync(FULL, k1);
+      const int c = __popc(s0) + __popc(s1);
+      int cnew = 0;
+      if (c > 0) {
+        bool sorted = false;
+        if (c <= 16) {
+          // rank of a survivor = number of survivors with a smaller key
+          int r0 = 0, r1 = 0;
+          bool d0 = false, d1 = false;
+          for (unsigned m = s0; m; m &= m - 1) {
+            const int src = __ffs(m) - 1;
+            const u64 x = __shfl_sync(FULL, e0, src);
+            r0 += x < e0;
+            r1 += x < e1;
+            d0 |= (x == e0) && (src < lane);
+            d1 |= x == e1;
           }
-          if (k1) {
-            ck[cs0 + __popc(s1 & lt)] = e1;
-            clb[cs0 + __popc(s1 & lt)] = lb1;
+          for (unsigned m = s1; m; m &= m - 1) {
+            const int src = __ffs(m) - 1;
+            const u64 x = __shfl_sync(FULL, e1, src);
+            r0 += x < e0;
+            r1 += x < e1;
+            d1 |= (x == e1) && (src < lane);
           }
-          __syncwarp();
-          const int lo = clb[0];
-          for (int top = len; top > lo; top -= 32) {
-            const int i = top - 32 + lane;
-            const bool act = i >= lo;
-            u64 val = 0;
-            int dest = 0;
-            if (act) {
-              val = W[i];
-              dest = i + count_le(clb, cnew, i);
+          // a key repeated inside the batch (possible only after the visited
+          // table forgot, with a repeated edge) takes the sorting path
+          if (__ballot_sync(FULL, (k0 && d0) || (k1 && d1)) == 0) {
+            __syncwarp();
+            if (k0) {
+              ck[r0] = e0;
+              clb[r0] = lb0;
             }
-            __syncwarp();
-            if (act && dest < ef) W[dest] = val;
-            __syncwarp();
+            if (k1) {
+              ck[r1] = e1;
+              clb[r1] = lb1;
+            }
+            cnew = c;
+            sorted = true;
           }
-          for (int j = lane; j < cnew; j += 32) {
-            const int pos = j + clb[j];
-            if (pos < ef) W[pos] = ck[j];
+        }
+        if (!sorted) cnew = order_by_sort(e0, e1, k0, k1, W, len, ck, clb, lane);
+        __syncwarp();
+        // merge: move W[lo..len) right by the number of survivors ranked before
+        // each entry, last chunk first, then drop the survivors in place
+        const int lo = clb[0];
+        for (int top = len; top > lo; top -= 32) {
+          const int i = top - 32 + lane;
+          const bool act = i >= lo;
+          u64 val = 0;
+          int dest = 0;
+          if (act) {
+            val = W[i];
+            dest = i + count_le(clb, cnew, i);
           }
           __syncwarp();
-          len = min(len + cnew, ef);
-          if (lo < cursor) cursor = lo;
+          if (act && dest < ef) W[dest] = val;
+          __syncwarp();
         }
+        for (int j = lane; j < cnew; j += 32) {
+          const int pos = j + clb[j];
+          if (pos < ef) W[pos] = ck[j];
+        }
+        __syncwarp();
+        len = min(len + cnew, ef);
+        if (lo < cursor) cursor = lo;
       }
     }
     // visited-table upkeep: keep the load factor at or below one half
     if (stored > (Hn >> 1)) {
       st |= KANN_QSTAT_FORGOT;
-      for (int i = lane; i < Hn; i += 32) H[i] = HEMPTY;
-      __syncwarp();
-      for (int i = lane; i < len; i += 32) visit(H, a.hbits, key_id(W[i]));
-      __syncwarp();
+      reset_visited(H, a.hbits, W, len, lane);
       stored = len;
     }
   }
@@ -574,24 +652,9 @@ __device__ __forceinline__ void search_one(const SearchArgs& a, B& be, int qi, i
   // 4. exact re-rank of the best R entries
   int nout = len;
   if (a.R != 0 && a.rr_data != nullptr) {
-    int R = a.R < 0 ? ef : a.R;
-    R = min(R, len);
-    const float* q = a.q + (size_t)qi * a.d;
-    for (int b = 0; b < R; b += 64) {
-      const int cb = min(64, R - b);
-      for (int j = lane; j < cb; j += 32) cid[j] = (int)key_id(W[b + j]);
-      __syncwarp();
-      rerank_dists<CPLR>(a, q, cid, cb, ck, lane);
-      __syncwarp();
-      for (int j = lane; j < cb; j += 32) W[b + j] = ck[j];
-      __syncwarp();
-    }
-    int P = 2;
-    while (P < R) P <<= 1;
-    for (int i = R + lane; i < P; i += 32) W[i] = KEY_MAX;
-    __syncwarp();
-    warp_smem_sort(W, P, lane);
-    nout = R;
+    const int R = min(a.R < 0 ? ef : a.R, len);
+    nout = rerank_phase(a.rr_data, a.rr_stride, a.rr_nchunks, a.rr_lpr, a.metric, a.q + (size_t)qi * a.d, R, W, ck,
+                        cid, lane);
   }
 
   // 5. output
@@ -619,31 +682,32 @@ __device__ __forceinline__ void search_one(const SearchArgs& a, B& be, int qi, i
   }
 }
 
-// Small rows (one chunk per lane) get a 64-register budget (32 warps per SM);
-// wider rows keep their query chunks in registers at 128.
-template <int CPLT, int CPLR>
+// Register budget from the query registers a lane holds: <= 8 -> 64
+// registers (32 warps per SM), <= 16 -> 80 (24 warps), wider -> 128.
+template <int DT, int CPLT>
 struct MinBlocks {
-  static constexpr int value = (CPLT <= 1 && CPLR <= 2) ? 8 : 4;
+  static constexpr int q = CPLT * Fmt<DT>::EPC;
+  static constexpr int value = q <= 8 ? 8 : (q <= 16 ? 6 : 4);
 };
 
-template <int DT, int CPLT, int CPLR>
-__global__ void __launch_bounds__(128, MinBlocks<CPLT, CPLR>::value) search_dense_kernel(const SearchArgs a) {
+template <int DT, int CPLT>
+__global__ void __launch_bounds__(128, MinBlocks<DT, CPLT>::value) search_dense_kernel(const SearchArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int qi = blockIdx.x * (blockDim.x >> 5) + warp;
   if (qi >= a.nq) return;
   DenseBackend<DT, CPLT> be;
-  search_one<DenseBackend<DT, CPLT>, CPLR>(a, be, qi, lane, smem + (size_t)warp * a.warp_smem);
+  search_one<DenseBackend<DT, CPLT>>(a, be, qi, lane, smem + (size_t)warp * a.warp_smem);
 }
 
-template <int CPLT, int CPLR>
+template <int CPLT>
 __global__ void __launch_bounds__(128, 1) search_pq_kernel(const SearchArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int qi = blockIdx.x * (blockDim.x >> 5) + warp;
   if (qi >= a.nq) return;
   PQBackend<CPLT> be;
-  search_one<PQBackend<CPLT>, CPLR>(a, be, qi, lane, smem + (size_t)warp * a.warp_smem);
+  search_one<PQBackend<CPLT>>(a, be, qi, lane, smem + (size_t)warp * a.warp_smem);
 }
 
 __global__ void __launch_bounds__(128, 4) search_sparse_kernel(const SearchArgs a, const __grid_constant__ SparseArgs sp) {
@@ -653,26 +717,20 @@ __global__ void __launch_bounds__(128, 4) search_sparse_kernel(const SearchArgs 
   if (qi >= a.nq) return;
   SparseBackend be;
   be.sp = &sp;
-  search_one<SparseBackend, 1>(a, be, qi, lane, smem + (size_t)warp * a.warp_smem);
+  search_one<SparseBackend>(a, be, qi, lane, smem + (size_t)warp * a.warp_smem);
 }
 
 typedef void (*KernelFn)(const SearchArgs);
 
 template <int DT>
-KernelFn pick_dense(int cplt, int cplr) {
-#define KANN_CASE(T, R) \
-  if (cplt == T && cplr == R) return search_dense_kernel<DT, T, R>;
-  KANN_CASE(1, 1)
-  KANN_CASE(1, 2)
-  KANN_CASE(1, 4)
-  KANN_CASE(2, 2)
-  KANN_CASE(2, 4)
-  KANN_CASE(2, 8)
-  KANN_CASE(4, 4)
-  KANN_CASE(4, 8)
-  KANN_CASE(8, 8)
-#undef KANN_CASE
-  return nullptr;
+KernelFn pick_dense(int cplt) {
+  switch (cplt) {
+    case 1: return search_dense_kernel<DT, 1>;
+    case 2: return search_dense_kernel<DT, 2>;
+    case 4: return search_dense_kernel<DT, 4>;
+    case 8: return search_dense_kernel<DT, 8>;
+    default: return nullptr;
+  }
 }
 
 int pow2_at_least(int x) {
@@ -690,14 +748,12 @@ int search_warp_smem(int efcap, int hbits) {
 int launch_search_dense(const SearchArgs& a, int dtype, int wpb, void* stream) {
   if (a.nq == 0) return 0;
   const int cplt = pow2_at_least((a.nchunks + a.lpr - 1) / a.lpr);
-  // the re-rank mapping is the one an FP32 traversal of the same d would use
-  const int cplr = a.rr_nchunks > 0 ? pow2_at_least((a.rr_nchunks + a.rr_lpr - 1) / a.rr_lpr) : cplt;
   KernelFn fn = nullptr;
   switch (dtype) {
-    case KANN_F32: fn = pick_dense<KANN_F32>(cplt, cplr < cplt ? cplt : cplr); break;
-    case KANN_F16: fn = pick_dense<KANN_F16>(cplt, cplr < cplt ? cplt : cplr); break;
-    case KANN_BF16: fn = pick_dense<KANN_BF16>(cplt, cplr < cplt ? cplt : cplr); break;
-    case KANN_E4M3: fn = pick_dense<KANN_E4M3>(cplt, cplr < cplt ? cplt : cplr); break;
+    case KANN_F32: fn = pick_dense<KANN_F32>(cplt); break;
+    case KANN_F16: fn = pick_dense<KANN_F16>(cplt); break;
+    case KANN_BF16: fn = pick_dense<KANN_BF16>(cplt); break;
+    case KANN_E4M3: fn = pick_dense<KANN_E4M3>(cplt); break;
     default: break;
   }
   if (!fn) return (int)cudaErrorInvalidValue;
@@ -716,14 +772,10 @@ int search_warp_smem_sparse(int efcap, int hbits) { return search_warp_smem(efca
 int launch_search_pq(const SearchArgs& a, int wpb, void* stream) {
   if (a.nq == 0) return 0;
   const int cplt = pow2_at_least((a.nchunks + a.lpr - 1) / a.lpr);
-  int cplr = a.rr_nchunks > 0 ? pow2_at_least((a.rr_nchunks + a.rr_lpr - 1) / a.rr_lpr) : 1;
   KernelFn fn = nullptr;
-#define KANN_PQ(T, R) \
-  if (cplt == T && cplr == R) fn = search_pq_kernel<T, R>;
-  KANN_PQ(1, 1) KANN_PQ(1, 2) KANN_PQ(1, 4) KANN_PQ(1, 8)
-  KANN_PQ(2, 1) KANN_PQ(2, 2) KANN_PQ(2, 4) KANN_PQ(2, 8)
-  KANN_PQ(4, 1) KANN_PQ(4, 2) KANN_PQ(4, 4) KANN_PQ(4, 8)
-#undef KANN_PQ
+  if (cplt == 1) fn = search_pq_kernel<1>;
+  if (cplt == 2) fn = search_pq_kernel<2>;
+  if (cplt == 4) fn = search_pq_kernel<4>;
   if (!fn) return (int)cudaErrorInvalidValue;
   const size_t smem = (size_t)wpb * a.warp_smem;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -59,8 +59,8 @@ class kann_sparse_desc(ctypes.Structure):
 
 class kann_search_opts(ctypes.Structure):
     _fields_ = [("rerank", ctypes.c_int32), ("max_hops", ctypes.c_int32), ("hash_bits", ctypes.c_int32),
-                ("warps_per_block", ctypes.c_int32), ("d_status", ctypes.c_void_p),
-                ("d_counters", ctypes.c_void_p)]
+                ("warps_per_block", ctypes.c_int32), ("lanes_per_row", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("d_status", ctypes.c_void_p), ("d_counters", ctypes.c_void_p)]
 
 
 _L = None
@@ -194,9 +194,9 @@ def kann_index_upload(graph, vectors=None, dtype=KANN_F32, metric=KANN_L2, scale
     return Index(h, keep, kind, d, metric)
 
 
-def _opts(rerank=0, max_hops=0, hash_bits=0, warps_per_block=0, status=None, counters=None):
+def _opts(rerank=0, max_hops=0, hash_bits=0, warps_per_block=0, lanes_per_row=0, status=None, counters=None):
     _require_cuda(status, counters)
-    return kann_search_opts(int(rerank), int(max_hops), int(hash_bits), int(warps_per_block),
+    return kann_search_opts(int(rerank), int(max_hops), int(hash_bits), int(warps_per_block), int(lanes_per_row), 0,
                             status.data_ptr() if status is not None else None,
                             counters.data_ptr() if counters is not None else None)
 
@@ -207,7 +207,7 @@ def kann_search(index, queries, k, ef, ids=None, dists=None, stream=None):
 
 def kann_search_ex(index, queries, k, ef, ids=None, dists=None, stream=None, **opts):
     """queries [n, d] float32 on the device -> (ids [n, k] int32, dists [n, k] float32).
-    opts: rerank, max_hops, hash_bits, warps_per_block, status ([n] int32
+    opts: rerank, max_hops, hash_bits, warps_per_block, lanes_per_row, status ([n] int32
     tensor, bits KANN_QSTAT_*), counters ([n, 4] int32 tensor)."""
     _require_cuda(queries)
     n = queries.shape[0]

@@ -243,8 +243,16 @@ def main():
     idx16 = K_.kann_index_upload(gd, vectors=Xh, dtype=K_.KANN_F16, metric=K_.KANN_L2, rerank=Xd)
     idx32 = K_.kann_index_upload(gd, vectors=Xd, dtype=K_.KANN_F32, metric=K_.KANN_L2)
     Qd = torch.from_numpy(Q).to(dev)
-    gt, _ = K_.kann_exact_knn(Qd, Xd, K, K_.KANN_L2)
+    # ground truth: tensor-core exact k-NN on BF16 copies (integers 0..255 are
+    # exact in BF16 and every dot product / norm stays below 2^24 in FP32)
+    Xb, _ = K_.kann_quantize(Xd, K_.KANN_BF16)
+    Qb, _ = K_.kann_quantize(Qd, K_.KANN_BF16)
     torch.cuda.synchronize()
+    tg = time.time()
+    gt, _ = K_.kann_exact_knn(Qb, Xb, K, K_.KANN_L2, dtype=K_.KANN_BF16)
+    torch.cuda.synchronize()
+    gt_s = time.time() - tg
+    del Xb
     gt = gt.cpu().numpy()
 
     # ---- ef sweep: smallest ef with recall@10 >= 0.95 (FP16 + re-rank)
@@ -370,6 +378,7 @@ def main():
                        "l2": "inputs larger than L2 (f16 base 256 MB + f32 base 512 MB + graph 256 MB)",
                        "fp32_plain_qps": N_QUERY * world / (fp32_ms / 1e3), "fp32_plain_ms_per_step": fp32_ms,
                        "ef_sweep": sweep, "graph_build_s": build_s, "graph_cached": cached,
+                       "ground_truth_s": gt_s,
                        "batch_latency_ms": {"p50": per_sorted[len(per) // 2],
                                             "p99": per_sorted[min(len(per) - 1, int(0.99 * len(per)))]},
                        "work_per_query": {"l0_dist": c[0], "l0_expansions": c[1], "upper_dist": c[2],

@@ -12,7 +12,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libkann.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
-CU_SOURCES = ["kann_api.cu", "kann_search.cu", "kann_exact.cu"]
+CU_SOURCES = ["kann_api.cu", "kann_search.cu", "kann_exact.cu", "kann_exact_tc.cu"]
 CPP_SOURCES = ["kann_build.cpp"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -31,14 +31,19 @@ def build(force=False, verbose=False):
     bdir = os.path.join(HERE, "_build")
     os.makedirs(bdir, exist_ok=True)
     objs = []
+    cmds = []
     for src in CU_SOURCES:
         obj = os.path.join(bdir, src + ".o")
         cmd = [NVCC, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE,
                "-c", os.path.join(CSRC, src), "-o", obj]
         if verbose:
             cmd.insert(1, "-Xptxas=-v")
-        subprocess.check_call(cmd)
+        cmds.append(cmd)
         objs.append(obj)
+    procs = [subprocess.Popen(c) for c in cmds]
+    codes = [p.wait() for p in procs]
+    if any(codes):
+        raise RuntimeError("nvcc failed: %s" % codes)
     for src in CPP_SOURCES:
         obj = os.path.join(bdir, src + ".o")
         subprocess.check_call(["g++", "-std=c++17", "-O3", "-fPIC", "-pthread", "-I" + INCLUDE, "-c",

@@ -196,9 +196,8 @@ int splits_for(int nq, int64_t nb) {
 using namespace kann;
 
 extern "C" size_t kann_exact_knn_workspace_bytes(int nq, int64_t nb, int d, int k, int dtype) {
-  (void)d;
-  (void)dtype;
   if (nq <= 0 || nb <= 0 || k <= 0) return 0;
+  if (exact_tc_supported(dtype, d, k)) return exact_tc_workspace_bytes(nq, nb, k);
   return (size_t)nq * splits_for(nq, nb) * k * sizeof(u64);
 }
 
@@ -213,6 +212,16 @@ extern "C" int kann_exact_knn(const void* d_queries, const void* d_base, int nq,
   if (!d_queries || !d_base || !d_ids || !d_dists || !d_ws) return KANN_EINVAL;
   if (nb == 0 || nb >= ((int64_t)1 << 31)) return KANN_EINVAL;
   if (ws_bytes < kann_exact_knn_workspace_bytes(nq, nb, d, k, dtype)) return KANN_EINVAL;
+  if (exact_tc_supported(dtype, d, k)) {
+    // BF16/FP16 inputs, k <= 32: tensor-core scores with the fused top-k
+    const int e = exact_tc_run(d_queries, d_base, nq, nb, d, metric, dtype, k, d_ids, d_dists, d_ws,
+                               (cudaStream_t)stream);
+    if (e != cudaSuccess) {
+      set_cuda_error(e);
+      return KANN_ECUDA;
+    }
+    return KANN_OK;
+  }
   const int S = splits_for(nq, nb);
   const int kp = (k + 31) / 32 * 32;
   const size_t smem = (size_t)(QT * LDS + BT * LDS + QT * (BT + 1)) * 4 + (size_t)QT * kp * 8;

@@ -1,0 +1,526 @@
+// kann_exact_tc.cu -- exact k-NN on the 5th-generation tensor cores (tcgen05).
+//
+// The ground truth for recall (the paper's k-NN problem, Sec. 1) over BF16 or
+// FP16 inputs: S = Q X^T accumulates in FP32 in tensor memory, the epilogue
+// turns a row of S into distances (L2: ||x||^2 - 2 q.x + ||q||^2, IP: -q.x)
+// and keeps each query's k best (distance, id) pairs in registers; the scores
+// are never written to HBM.
+//
+// One persistent CTA per SM walks work items (a tile of 128 queries x one
+// split of the base).  Roles inside a CTA (192 threads):
+//   warp 0      TMA producer: per base tile of 256 rows and per 64-element K
+//               chunk, loads the query chunk (128 x 64) and the base chunk
+//               (256 x 64), 128-byte swizzled, into a 4-stage ring;
+//   warp 1      allocates 512 TMEM columns (two 128 x 256 FP32 accumulators)
+//               and issues tcgen05.mma (M=128, N=256, K=16) from one lane;
+//               tcgen05.commit frees a ring stage when its MMAs are done and
+//               signals a full accumulator;
+//   warps 2..5  epilogue warpgroup: thread r owns query row r (TMEM lane r),
+//               reads its 256 scores with tcgen05.ld, filters them against its
+//               current k-th distance and inserts the survivors.
+// Accumulators are double-buffered so the epilogue of tile t overlaps the
+// MMAs of tile t+1.  Every mbarrier wait is bounded by a %globaltimer
+// deadline; on expiry the CTA raises an error flag and all roles wind down,
+// and the merge pass then reports id -1 for every query.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+#include "kann_device.cuh"
+#include "kann_internal.h"
+
+namespace kann {
+namespace {
+
+constexpr int TC_M = 128;       // queries per work item (TMEM lanes)
+constexpr int TC_N = 256;       // base rows per tile (accumulator columns)
+constexpr int TC_K = 64;        // K elements per stage: one 128-byte swizzle row
+constexpr int TC_STAGES = 4;
+constexpr int A_BYTES = TC_M * TC_K * 2;
+constexpr int B_BYTES = TC_N * TC_K * 2;
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int TC_THREADS = 192;
+constexpr uint32_t TMEM_COLS = 512;
+constexpr int TC_KMAX = 32;     // largest k kept in registers by the epilogue
+constexpr unsigned long long WAIT_NS = 2000000000ull;  // 2 s per wait
+
+struct TcArgs {
+  int nq;
+  int64_t nb;
+  int d, metric, k, S, kchunks;
+  int64_t per;          // base rows per split (a multiple of TC_N)
+  int n_items;
+  uint32_t idesc;
+  const float* xnorm;   // [nb]
+  const float* qnorm;   // [nq]
+  u64* out;             // [nq][S][k] partial lists
+  int* err;
+};
+
+// ---- PTX wrappers ----------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+// Wait for the phase of `bar` with the given parity; false if the deadline
+// passed or another role raised the error flag.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err) {
+  unsigned long long t0 = 0;
+  for (uint32_t it = 0;; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    if ((it & 255u) == 255u) {
+      if (*(volatile int*)err) return false;
+      const unsigned long long t = gtimer();
+      if (t0 == 0) t0 = t;
+      else if (t - t0 > WAIT_NS) {
+        atomicOr(err, 1);
+        return false;
+      }
+    }
+  }
+}
+
+// The same wait taken by a whole warp with one outcome for every lane.
+__device__ __forceinline__ bool mbar_wait_warp(uint32_t bar, uint32_t parity, int* err, int lane) {
+  unsigned long long t0 = 0;
+  for (uint32_t it = 0;; ++it) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (__all_sync(FULL, ok)) return true;
+    if ((it & 255u) == 255u) {
+      int stop = 0;
+      if (lane == 0) {
+        if (*(volatile int*)err) stop = 1;
+        const unsigned long long t = gtimer();
+        if (t0 == 0) t0 = t;
+        else if (t - t0 > WAIT_NS) {
+          atomicOr(err, 1);
+          stop = 1;
+        }
+      }
+      if (__shfl_sync(FULL, stop, 0)) return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(dst),
+      "l"(map), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor of a K-major operand staged with the
+// 128-byte swizzle: rows of 128 bytes, 8-row groups 1024 bytes apart.
+__device__ __forceinline__ u64 smem_desc(uint32_t saddr) {
+  u64 d = 0;
+  d |= (u64)((saddr & 0x3FFFFu) >> 4);   // start address
+  d |= (u64)(16u >> 4) << 16;            // leading byte offset (unused with this swizzle)
+  d |= (u64)(1024u >> 4) << 32;          // stride byte offset: next 8-row group
+  d |= (u64)1 << 46;                     // descriptor version for tcgen05
+  d |= (u64)2 << 61;                     // 128-byte swizzle
+  return d;
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t dtmem, u64 adesc, u64 bdesc, uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// 64 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tc_ld64(uint32_t taddr, float* v) {
+  uint32_t r[64];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x64.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,"
+      "%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,"
+      "%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]),
+        "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]),
+        "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]),
+        "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]),
+        "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 64; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// ---- the kernel ------------------------------------------------------------
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    exact_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ CUtensorMap tmX, const TcArgs a) {
+  extern __shared__ unsigned char smem_raw[];
+  // 1024-byte alignment for the swizzled stages
+  unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* stage_base = smem;
+  u64* bars = reinterpret_cast<u64*>(smem + TC_STAGES * STAGE_BYTES);
+  // bars: full[STAGES], empty[STAGES], tfull[2], tempty[2]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * TC_STAGES + 4);
+  float* xn_s = reinterpret_cast<float*>(tmem_slot + 4);  // [4][TC_N] per-warp tile norms
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + TC_STAGES);
+  const uint32_t tfull0 = smem_u32(bars + 2 * TC_STAGES), tempty0 = smem_u32(bars + 2 * TC_STAGES + 2);
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < TC_STAGES; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(tfull0 + 8 * b, 1);
+      mbar_init(tempty0 + 8 * b, 4);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    // ---------------- TMA producer ----------------
+    if (lane == 0) {
+      uint32_t it = 0;
+      bool ok = true;
+      for (int item = blockIdx.x; item < a.n_items && ok; item += gridDim.x) {
+        const int q0 = (item / a.S) * TC_M;
+        const int64_t b_begin = (int64_t)(item % a.S) * a.per;
+        const int64_t b_end = b_begin + a.per < a.nb ? b_begin + a.per : a.nb;
+        for (int64_t b0 = b_begin; b0 < b_end && ok; b0 += TC_N) {
+          for (int kc = 0; kc < a.kchunks && ok; ++kc, ++it) {
+            const uint32_t s = it % TC_STAGES, ph = (it / TC_STAGES) & 1u;
+            ok = mbar_wait(empty0 + 8 * s, ph ^ 1u, a.err);
+            if (!ok) break;
+            const uint32_t sa = smem_u32(stage_base + s * STAGE_BYTES);
+            mbar_expect_tx(full0 + 8 * s, STAGE_BYTES);
+            tma_load_2d(sa, &tmQ, kc * TC_K, q0, full0 + 8 * s);
+            tma_load_2d(sa + A_BYTES, &tmX, kc * TC_K, (int)b0, full0 + 8 * s);
+          }
+        }
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer (one lane) ----------------
+    if (lane == 0) {
+      uint32_t it = 0, t = 0;
+      bool ok = true;
+      for (int item = blockIdx.x; item < a.n_items && ok; item += gridDim.x) {
+        const int64_t b_begin = (int64_t)(item % a.S) * a.per;
+        const int64_t b_end = b_begin + a.per < a.nb ? b_begin + a.per : a.nb;
+        for (int64_t b0 = b_begin; b0 < b_end && ok; b0 += TC_N, ++t) {
+          const uint32_t buf = t & 1u, use = t >> 1;
+          ok = mbar_wait(tempty0 + 8 * buf, (use & 1u) ^ 1u, a.err);
+          if (!ok) break;
+          tc_fence_after();
+          const uint32_t dt = tmem + buf * TC_N;
+          for (int kc = 0; kc < a.kchunks; ++kc, ++it) {
+            const uint32_t s = it % TC_STAGES, ph = (it / TC_STAGES) & 1u;
+            ok = mbar_wait(full0 + 8 * s, ph, a.err);
+            if (!ok) break;
+            tc_fence_after();
+            const uint32_t sa = smem_u32(stage_base + s * STAGE_BYTES);
+#pragma unroll
+            for (int kk = 0; kk < TC_K / 16; ++kk)
+              tc_mma(dt, smem_desc(sa + kk * 32), smem_desc(sa + A_BYTES + kk * 32), a.idesc, (kc | kk) != 0);
+            tc_commit(empty0 + 8 * s);
+          }
+          if (!ok) break;
+          tc_commit(tfull0 + 8 * buf);
+        }
+      }
+    }
+  } else {
+    // ---------------- epilogue warpgroup ----------------
+    const int quarter = warp & 3;            // TMEM lanes 32*quarter .. +31
+    const int row = quarter * 32 + lane;
+    float* xw = xn_s + (warp - 2) * TC_N;    // this warp's copy of the tile's norms
+    uint32_t t = 0;
+    bool ok = true;
+    for (int item = blockIdx.x; item < a.n_items && ok; item += gridDim.x) {
+      const int q = (item / a.S) * TC_M + row;
+      const int split = item % a.S;
+      const int64_t b_begin = (int64_t)split * a.per;
+      const int64_t b_end = b_begin + a.per < a.nb ? b_begin + a.per : a.nb;
+      float kd[TC_KMAX];
+      int ki[TC_KMAX];
+#pragma unroll
+      for (int j = 0; j < TC_KMAX; ++j) {
+        kd[j] = j < a.k ? __int_as_float(0x7f800000) : -__int_as_float(0x7f800000);
+        ki[j] = -1;
+      }
+      float thr = __int_as_float(0x7f800000);
+      int worst = 0;
+      for (int64_t b0 = b_begin; b0 < b_end; b0 += TC_N, ++t) {
+        const uint32_t buf = t & 1u, use = t >> 1;
+        if (a.metric == KANN_L2)
+          for (int j = lane; j < TC_N; j += 32) xw[j] = (b0 + j < b_end) ? __ldg(a.xnorm + b0 + j) : 0.f;
+        __syncwarp();
+        ok = mbar_wait_warp(tfull0 + 8 * buf, use & 1u, a.err, lane);
+        if (!ok) break;
+        tc_fence_after();
+        for (int c0 = 0; c0 < TC_N; c0 += 64) {
+          float v[64];
+          tc_ld64(tmem + ((uint32_t)(quarter * 32) << 16) + buf * TC_N + c0, v);
+#pragma unroll 4
+          for (int j = 0; j < 64; ++j) {
+            const int64_t col = b0 + c0 + j;
+            const float dist = a.metric == KANN_L2 ? fmaf(-2.f, v[j], xw[c0 + j]) : -v[j];
+            if (dist < thr && col < b_end) {
+              // replace the worst entry, then find the new worst by (d, id);
+              // columns arrive in increasing id order, so a tie never enters
+#pragma unroll
+              for (int m = 0; m < TC_KMAX; ++m)
+                if (m == worst) {
+                  kd[m] = dist;
+                  ki[m] = (int)col;
+                }
+              float wd = -__int_as_float(0x7f800000);
+              int wid = -2, wi = 0;
+#pragma unroll
+              for (int m = 0; m < TC_KMAX; ++m) {
+                if (m < a.k && (kd[m] > wd || (kd[m] == wd && ki[m] > wid))) {
+                  wd = kd[m];
+                  wid = ki[m];
+                  wi = m;
+                }
+              }
+              thr = wd;
+              worst = wi;
+            }
+          }
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(tempty0 + 8 * buf);
+      }
+      if (!ok) break;
+      if (q < a.nq) {
+        const float qn = a.metric == KANN_L2 ? a.qnorm[q] : 0.f;
+        u64* o = a.out + ((size_t)q * a.S + split) * a.k;
+#pragma unroll
+        for (int j = 0; j < TC_KMAX; ++j)
+          if (j < a.k) o[j] = ki[j] < 0 ? ((u64)ordered_bits(__int_as_float(0x7f800000)) << 32) | 0xffffffffull
+                                        : make_key(kd[j] + qn, (uint32_t)ki[j]);
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+  }
+}
+
+// Squared norms of BF16/FP16 rows in FP32 (one warp per row).
+template <int DT>
+__global__ void row_norms_kernel(const uint16_t* __restrict__ x, int64_t n, int d, float* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (row >= n) return;
+  float s = 0.f;
+  for (int k = lane * 8; k < d; k += 256) {
+    const uint4 w = *reinterpret_cast<const uint4*>(x + row * d + k);
+    float v[8];
+    Fmt<DT>::unpack(w, v);
+#pragma unroll
+    for (int e = 0; e < 8; ++e) s = fmaf(v[e], v[e], s);
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
+  if (lane == 0) out[row] = s;
+}
+
+// Final merge: sort each query's S*k partial keys, keep k (an error flag
+// from the main pass turns every output into id -1 / +inf).
+__global__ void exact_tc_merge_kernel(const u64* __restrict__ ws, const int* err, int nq, int S, int k, int P,
+                                      int32_t* ids, float* dists) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int q = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (q >= nq) return;
+  const bool bad = *err != 0;
+  u64* A = reinterpret_cast<u64*>(smem) + (size_t)warp * P;
+  const int tot = S * k;
+  for (int i = lane; i < P; i += 32) A[i] = (i < tot && !bad) ? ws[(size_t)q * tot + i] : KEY_MAX;
+  __syncwarp();
+  warp_smem_sort(A, P, lane);
+  for (int j = lane; j < k; j += 32) {
+    const u64 key = A[j];
+    const uint32_t id = (uint32_t)key;
+    ids[(size_t)q * k + j] = (key == KEY_MAX || id == 0xffffffffu) ? -1 : (int32_t)id;
+    dists[(size_t)q * k + j] = (key == KEY_MAX || id == 0xffffffffu) ? __int_as_float(0x7f800000) : key_dist(key);
+  }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 get_encode() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+bool make_map(CUtensorMap* m, const void* base, int dtype, int d, int64_t rows, int box_rows) {
+  auto enc = get_encode();
+  if (!enc) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)d, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)d * 2};
+  const cuuint32_t box[2] = {(cuuint32_t)TC_K, (cuuint32_t)box_rows};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUtensorMapDataType t = dtype == KANN_BF16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+  return enc(m, t, 2, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Instruction descriptor of tcgen05.mma kind::f16: FP32 accumulator, A and B
+// in the same 16-bit format, both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+uint32_t make_idesc(int dtype) {
+  const uint32_t ab = dtype == KANN_BF16 ? 1u : 0u;
+  return (1u << 4) | (ab << 7) | (ab << 10) | ((uint32_t)(TC_N >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
+}
+
+int num_sms() {
+  int dev = 0, n = 148;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  return n;
+}
+
+}  // namespace
+
+// Work split of the tensor-core path: queries in tiles of 128, the base in S
+// splits (multiples of 256 rows) so that there are >= 4 work items per SM.
+void exact_tc_plan(int nq, int64_t nb, int* S_out, int64_t* per_out) {
+  const int qtiles = (nq + TC_M - 1) / TC_M;
+  const int64_t ntiles = (nb + TC_N - 1) / TC_N;
+  int S = (4 * 148 + qtiles - 1) / qtiles;
+  if (S > 64) S = 64;
+  if (S > ntiles) S = (int)ntiles;
+  if (S < 1) S = 1;
+  const int64_t tiles_per = (ntiles + S - 1) / S;
+  S = (int)((ntiles + tiles_per - 1) / tiles_per);
+  *S_out = S;
+  *per_out = tiles_per * TC_N;
+}
+
+size_t exact_tc_workspace_bytes(int nq, int64_t nb, int k) {
+  int S;
+  int64_t per;
+  exact_tc_plan(nq, nb, &S, &per);
+  return (size_t)nq * S * k * 8 + (size_t)nb * 4 + (size_t)nq * 4 + 256;
+}
+
+bool exact_tc_supported(int dtype, int d, int k) {
+  return (dtype == KANN_BF16 || dtype == KANN_F16) && d % 8 == 0 && k >= 1 && k <= TC_KMAX;
+}
+
+int exact_tc_run(const void* Q, const void* X, int nq, int64_t nb, int d, int metric, int dtype, int k, int32_t* ids,
+                 float* dists, void* ws, cudaStream_t s) {
+  int S;
+  int64_t per;
+  exact_tc_plan(nq, nb, &S, &per);
+  unsigned char* w = static_cast<unsigned char*>(ws);
+  u64* part = reinterpret_cast<u64*>(w);
+  float* xn = reinterpret_cast<float*>(w + (size_t)nq * S * k * 8);
+  float* qn = xn + nb;
+  int* err = reinterpret_cast<int*>(((uintptr_t)(qn + nq) + 15) & ~(uintptr_t)15);
+  CUtensorMap mq, mx;
+  if (!make_map(&mq, Q, dtype, d, nq, TC_M) || !make_map(&mx, X, dtype, d, nb, TC_N)) return (int)cudaErrorInvalidValue;
+  cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), s);
+  if (e != cudaSuccess) return (int)e;
+  void (*nfn)(const uint16_t*, int64_t, int, float*) =
+      dtype == KANN_BF16 ? row_norms_kernel<KANN_BF16> : row_norms_kernel<KANN_F16>;
+  nfn<<<(unsigned)((nb * 32 + 255) / 256), 256, 0, s>>>((const uint16_t*)X, nb, d, xn);
+  nfn<<<(unsigned)(((int64_t)nq * 32 + 255) / 256), 256, 0, s>>>((const uint16_t*)Q, nq, d, qn);
+  TcArgs a;
+  a.nq = nq;
+  a.nb = nb;
+  a.d = d;
+  a.metric = metric;
+  a.k = k;
+  a.S = S;
+  a.kchunks = (d + TC_K - 1) / TC_K;
+  a.per = per;
+  a.n_items = ((nq + TC_M - 1) / TC_M) * S;
+  a.idesc = make_idesc(dtype);
+  a.xnorm = xn;
+  a.qnorm = qn;
+  a.out = part;
+  a.err = err;
+  const size_t smem = 1024 + (size_t)TC_STAGES * STAGE_BYTES + (2 * TC_STAGES + 4) * 8 + 16 + 4 * TC_N * 4;
+  e = cudaFuncSetAttribute(exact_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return (int)e;
+  const int grid = a.n_items < num_sms() ? a.n_items : num_sms();
+  exact_tc_kernel<<<grid, TC_THREADS, smem, s>>>(mq, mx, a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return (int)e;
+  int P = 32;
+  while (P < S * k) P <<= 1;
+  int wpb = 4;
+  while (wpb > 1 && (size_t)wpb * P * 8 > 160 * 1024) wpb >>= 1;
+  const size_t msmem = (size_t)wpb * P * 8;
+  e = cudaFuncSetAttribute(exact_tc_merge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msmem);
+  if (e != cudaSuccess) return (int)e;
+  exact_tc_merge_kernel<<<(nq + wpb - 1) / wpb, wpb * 32, msmem, s>>>(part, err, nq, S, k, P, ids, dists);
+  return (int)cudaGetLastError();
+}
+
+}  // namespace kann

@@ -3,6 +3,8 @@
 #include <cstddef>
 #include <cstdint>
 
+#include <cuda_runtime.h>
+
 #include "../../include/kann.h"
 
 namespace kann {
@@ -39,6 +41,8 @@ struct SearchArgs {
   int32_t* counters;
   int hbits, max_hops;
   int lpr_override;  // 0 = automatic lanes per row
+  int* work_counter;     // persistent mode: next query index (zeroed before launch), or null
+  const int32_t* d_n;    // persistent mode: device-side query count (<= nq), or null
   int efcap;       // W capacity (power of two >= efmax, >= 32)
   int warp_smem;   // bytes of shared memory per warp
 };
@@ -65,5 +69,11 @@ int launch_search_pq(const SearchArgs& a, int wpb, void* stream);
 int launch_search_sparse(const SearchArgs& a, const SparseArgs& s, int wpb, void* stream);
 
 void set_cuda_error(int e);
+
+// Tensor-core exact k-NN (kann_exact_tc.cu).
+bool exact_tc_supported(int dtype, int d, int k);
+size_t exact_tc_workspace_bytes(int nq, int64_t nb, int k);
+int exact_tc_run(const void* Q, const void* X, int nq, int64_t nb, int d, int metric, int dtype, int k, int32_t* ids,
+                 float* dists, void* ws, cudaStream_t s);
 
 }  // namespace kann

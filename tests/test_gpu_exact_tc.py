@@ -1,0 +1,70 @@
+"""Tensor-core (tcgen05) exact k-NN against the FP64 oracle's brute force.
+
+BF16/FP16 inputs with k <= 32 take the tensor-core path: S = Q X^T in FP32
+in tensor memory, distances ||x||^2 - 2 q.x + ||q||^2 (L2) or -q.x (IP),
+fused top-k.  On integer data small enough that every product and partial
+sum is an exact FP32 integer, the results must equal the oracle bit for bit;
+on real-valued data the oracle runs on the same BF16-rounded values and
+distances must agree within 1e-5 of sum |terms|."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from helpers import id_set_match_fraction
+from paper_2501_06121_b300 import kann as K
+
+pytestmark = pytest.mark.gpu
+
+
+def to16(a, dtype):
+    t = torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
+    return t.to(torch.bfloat16 if dtype == K.KANN_BF16 else torch.float16)
+
+
+@pytest.mark.parametrize("nq,nb,d,hi", [(300, 5000, 128, 256), (1, 1000, 64, 256), (129, 777, 768, 64),
+                                        (1000, 20000, 128, 256), (5, 300, 16, 256)])
+@pytest.mark.parametrize("dtype", [K.KANN_BF16, K.KANN_F16])
+def test_tc_exact_integer_data_bit_exact(nq, nb, d, hi, dtype):
+    rng = np.random.default_rng(nq + nb + d)
+    X = rng.integers(0, hi, (nb, d)).astype(np.float32)
+    Q = rng.integers(0, hi, (nq, d)).astype(np.float32)
+    k = min(10, nb)
+    gi, gd = K.kann_exact_knn(to16(Q, dtype), to16(X, dtype), k, K.KANN_L2, dtype=dtype)
+    torch.cuda.synchronize()
+    oi, od = O.exact_dense(X, Q, k, O.L2)
+    assert np.array_equal(gi.cpu().numpy(), oi)
+    assert np.array_equal(gd.cpu().numpy().astype(np.float64), od)
+
+
+@pytest.mark.parametrize("k", [1, 10, 32])
+@pytest.mark.parametrize("metric", [K.KANN_L2, K.KANN_IP])
+def test_tc_exact_real_data(k, metric):
+    rng = np.random.default_rng(k + 7 * metric)
+    Xb = to16(rng.standard_normal((30000, 128)), K.KANN_BF16)
+    Qb = to16(rng.standard_normal((500, 128)), K.KANN_BF16)
+    X = Xb.float().cpu().numpy()
+    Q = Qb.float().cpu().numpy()
+    gi, gd = K.kann_exact_knn(Qb, Xb, k, metric, dtype=K.KANN_BF16)
+    torch.cuda.synchronize()
+    gi, gd = gi.cpu().numpy(), gd.cpu().numpy()
+    oi, od = O.exact_dense(X, Q, k, metric)
+    assert id_set_match_fraction(gi, oi) >= 0.99
+    ref = O.dist_dense(X, Q, gi, metric)
+    if metric == K.KANN_L2:
+        mag = np.einsum("qd,qkd->qk", Q.astype(np.float64) ** 2, np.ones_like(X[gi], np.float64)) + \
+            np.einsum("qkd->qk", X.astype(np.float64)[gi] ** 2) + \
+            2 * np.einsum("qd,qkd->qk", np.abs(Q.astype(np.float64)), np.abs(X.astype(np.float64)[gi]))
+    else:
+        mag = np.einsum("qd,qkd->qk", np.abs(Q.astype(np.float64)), np.abs(X.astype(np.float64)[gi]))
+    assert np.all(np.abs(gd - ref) <= 1e-5 * np.maximum(np.abs(ref), mag))
+
+
+def test_large_k_falls_back_to_cuda_cores():
+    rng = np.random.default_rng(3)
+    X = rng.integers(0, 256, (4000, 64)).astype(np.float32)
+    Q = rng.integers(0, 256, (50, 64)).astype(np.float32)
+    gi, gd = K.kann_exact_knn(to16(Q, K.KANN_BF16), to16(X, K.KANN_BF16), 40, K.KANN_L2, dtype=K.KANN_BF16)
+    torch.cuda.synchronize()
+    oi, od = O.exact_dense(X, Q, 40, O.L2)
+    assert np.array_equal(gi.cpu().numpy(), oi)

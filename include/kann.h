@@ -152,11 +152,20 @@ typedef struct {
   int32_t hash_bits;       /* log2 of the per-query visited table; 0 = automatic */
   int32_t warps_per_block; /* queries per CTA (one warp each); 0 = automatic */
   int32_t lanes_per_row;   /* lanes sharing one row gather (power of two <= 32); 0 = automatic */
-  int32_t reserved;
+  int32_t prefetch;        /* 1 = L2-prefetch the adjacency row of every entry that enters W;
+                              0 = automatic (off: measured no gain on the 1M x 128 workload);
+                              -1 = off */
   uint32_t* d_status;      /* [n] per-query KANN_QSTAT_* bits, nullable */
   int32_t* d_counters;     /* [n][4] per-query counters, nullable: layer-0 distance
                               evaluations, layer-0 expansions, upper-layer distance
                               evaluations, upper-layer hops */
+  int32_t* d_work_counter; /* non-null: persistent work-stealing launch (one CTA set per SM,
+                              each warp takes the next query from this device counter,
+                              which the call zeroes on `stream` first); null: one warp per
+                              query in a plain grid */
+  const int32_t* d_n;      /* persistent mode only, nullable: device int holding the number
+                              of queries to run (clamped to n), read by the kernel -- lets a
+                              captured CUDA graph serve batches of varying size */
 } kann_search_opts;
 
 /* HNSW K-NN-SEARCH (Malkov & Yashunin Alg. 5) for n dense FP32 queries
@@ -230,6 +239,22 @@ int kann_exact_knn_noalloc(const void* d_queries, const void* d_base, int nq, in
  * RNE_satfinite(x / s) into d_out [n][d] uint8 and d_scale [n] (an all-zero
  * row gets s = 0 and zero codes).  Asynchronous on `stream`. */
 int kann_quantize(const float* d_x, int64_t n, int d, int dtype, void* d_out, float* d_scale, void* stream);
+
+/* ---- PQ codebooks (device) -------------------------------------------------
+ * Product Quantization (Sec. 2, citing Jegou et al.) as index preparation:
+ * kann_pq_train runs `iters` Lloyd iterations per subspace (m subspaces of
+ * dsub = d / m <= 16 dims, 256 centroids each) on FP32 rows d_x [n][d]
+ * (n >= 256), starting from 256 distinct training rows per subspace drawn by
+ * a counter-based SplitMix64 keyed by (seed, subspace, draw); a centroid
+ * that loses all its points keeps its position.  Writes d_codebooks
+ * [m][256][dsub]; d_ws is caller scratch of kann_pq_train_workspace_bytes.
+ * kann_pq_encode writes d_codes [n][m]: nearest centroid per subspace under
+ * L2 in FP32, ties to the lowest index.  Both are asynchronous on `stream`. */
+size_t kann_pq_train_workspace_bytes(int d, int m);
+int kann_pq_train(const float* d_x, int64_t n, int d, int m, int iters, uint64_t seed, float* d_codebooks, void* d_ws,
+                  size_t ws_bytes, void* stream);
+int kann_pq_encode(const float* d_x, int64_t n, int d, int m, const float* d_codebooks, uint8_t* d_codes,
+                   void* stream);
 
 /* ---- graph construction (host, multi-threaded) ---------------------------
  * The indexing pipeline of the paper (Sec. 2, Fig. 1) ends in an HNSW graph;

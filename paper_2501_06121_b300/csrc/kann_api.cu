@@ -142,6 +142,7 @@ int fill_search_args(const kann_index_t* idx, const float* d_q, int n, int k, in
   a.out_ids = d_ids;
   a.out_d = d_dists;
   a.max_hops = 1000000;
+  a.prefetch = 0;
   int hbits = 0;
   wpb = 4;
   int R = 0;
@@ -157,8 +158,13 @@ int fill_search_args(const kann_index_t* idx, const float* d_q, int n, int k, in
     const int l = opts->lanes_per_row;
     if (l < 0 || l > 32 || (l & (l - 1)) != 0) return KANN_EINVAL;
     a.lpr_override = l;
+    if (opts->prefetch < -1 || opts->prefetch > 1) return KANN_EINVAL;
+    a.prefetch = opts->prefetch > 0 ? 1 : 0;
     R = opts->rerank;
     if (R < -1) return KANN_EINVAL;
+    a.work_counter = opts->d_work_counter;
+    a.d_n = opts->d_n;
+    if (a.d_n && !a.work_counter) return KANN_EINVAL;
   }
   if (R != 0) {
     if (!idx->has_rr) return KANN_EINVAL;

@@ -43,6 +43,7 @@ struct SearchArgs {
   int lpr_override;  // 0 = automatic lanes per row
   int* work_counter;     // persistent mode: next query index (zeroed before launch), or null
   const int32_t* d_n;    // persistent mode: device-side query count (<= nq), or null
+  int prefetch;          // L2-prefetch the adjacency rows of new W entries
   int efcap;       // W capacity (power of two >= efmax, >= 32)
   int warp_smem;   // bytes of shared memory per warp
 };

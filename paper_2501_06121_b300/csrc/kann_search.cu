@@ -58,6 +58,11 @@ __device__ __forceinline__ int visit(uint32_t* H, int hbits, uint32_t id) {
   return 2;
 }
 
+// Bulk prefetch of `bytes` (a multiple of 16, 16-byte aligned) into L2.
+__device__ __forceinline__ void prefetch_l2(const void* p, int bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 __device__ __forceinline__ int lower_bound_w(const u64* W, int len, u64 key) {
   int lo = 0, hi = len;
   while (lo < hi) {
@@ -634,7 +639,12 @@ __device__ __forceinline__ void search_one(const SearchArgs& a, B& be, int qi, i
         }
         for (int j = lane; j < cnew; j += 32) {
           const int pos = j + clb[j];
-          if (pos < ef) W[pos] = ck[j];
+          if (pos < ef) {
+            W[pos] = ck[j];
+            // a new entry of W is likely to be expanded soon: start pulling its
+            // adjacency row into L2 now, so that expansion waits on L2, not DRAM
+            if (a.prefetch) prefetch_l2(a.l0 + (int64_t)key_id(ck[j]) * a.M0, a.M0 * 4);
+          }
         }
         __syncwarp();
         len = min(len + cnew, ef);
@@ -690,34 +700,47 @@ struct MinBlocks {
   static constexpr int value = q <= 8 ? 8 : (q <= 16 ? 6 : 4);
 };
 
-template <int DT, int CPLT>
-__global__ void __launch_bounds__(128, MinBlocks<DT, CPLT>::value) search_dense_kernel(const SearchArgs a) {
+// Queries of one launch: a plain grid gives warp w of CTA b query
+// b * warps + w; the persistent form has every warp take the next query index
+// from a device counter until the batch is exhausted (work stealing: a warp
+// that finishes a cheap query starts the next one at once).
+template <class B>
+__device__ __forceinline__ void run_queries(const SearchArgs& a, B& be) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int qi = blockIdx.x * (blockDim.x >> 5) + warp;
-  if (qi >= a.nq) return;
+  unsigned char* ws = smem + (size_t)warp * a.warp_smem;
+  if (a.work_counter == nullptr) {
+    const int qi = blockIdx.x * (blockDim.x >> 5) + warp;
+    if (qi < a.nq) search_one<B>(a, be, qi, lane, ws);
+    return;
+  }
+  int nq = a.nq;
+  if (a.d_n) nq = min(nq, max(0, *a.d_n));
+  for (;;) {
+    int qi = 0;
+    if (lane == 0) qi = atomicAdd(a.work_counter, 1);
+    qi = __shfl_sync(FULL, qi, 0);
+    if (qi >= nq) break;
+    search_one<B>(a, be, qi, lane, ws);
+  }
+}
+
+template <int DT, int CPLT>
+__global__ void __launch_bounds__(128, MinBlocks<DT, CPLT>::value) search_dense_kernel(const SearchArgs a) {
   DenseBackend<DT, CPLT> be;
-  search_one<DenseBackend<DT, CPLT>>(a, be, qi, lane, smem + (size_t)warp * a.warp_smem);
+  run_queries(a, be);
 }
 
 template <int CPLT>
 __global__ void __launch_bounds__(128, 1) search_pq_kernel(const SearchArgs a) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int qi = blockIdx.x * (blockDim.x >> 5) + warp;
-  if (qi >= a.nq) return;
   PQBackend<CPLT> be;
-  search_one<PQBackend<CPLT>>(a, be, qi, lane, smem + (size_t)warp * a.warp_smem);
+  run_queries(a, be);
 }
 
 __global__ void __launch_bounds__(128, 4) search_sparse_kernel(const SearchArgs a, const __grid_constant__ SparseArgs sp) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int qi = blockIdx.x * (blockDim.x >> 5) + warp;
-  if (qi >= a.nq) return;
   SparseBackend be;
   be.sp = &sp;
-  search_one<SparseBackend>(a, be, qi, lane, smem + (size_t)warp * a.warp_smem);
+  run_queries(a, be);
 }
 
 typedef void (*KernelFn)(const SearchArgs);
@@ -731,6 +754,26 @@ KernelFn pick_dense(int cplt) {
     case 8: return search_dense_kernel<DT, 8>;
     default: return nullptr;
   }
+}
+
+// Grid of a launch: one warp per query, or (persistent) as many CTAs as fit
+// on the GPU at once.
+template <class F>
+int launch_grid(F fn, const SearchArgs& a, int wpb, size_t smem) {
+  const int plain = (a.nq + wpb - 1) / wpb;
+  if (a.work_counter == nullptr) return plain;
+  int dev = 0, sms = 148, per_sm = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, wpb * 32, smem) != cudaSuccess || per_sm < 1)
+    per_sm = 1;
+  const int full = sms * per_sm;
+  return plain < full ? plain : full;
+}
+
+int start_counter(const SearchArgs& a, cudaStream_t s) {
+  if (a.work_counter == nullptr) return 0;
+  return (int)cudaMemsetAsync(a.work_counter, 0, sizeof(int), s);
 }
 
 int pow2_at_least(int x) {
@@ -760,7 +803,9 @@ int launch_search_dense(const SearchArgs& a, int dtype, int wpb, void* stream) {
   const size_t smem = (size_t)wpb * a.warp_smem;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return (int)e;
-  const int grid = (a.nq + wpb - 1) / wpb;
+  const int grid = launch_grid(fn, a, wpb, smem);
+  int c = start_counter(a, (cudaStream_t)stream);
+  if (c) return c;
   fn<<<grid, wpb * 32, smem, (cudaStream_t)stream>>>(a);
   return (int)cudaGetLastError();
 }
@@ -780,7 +825,10 @@ int launch_search_pq(const SearchArgs& a, int wpb, void* stream) {
   const size_t smem = (size_t)wpb * a.warp_smem;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return (int)e;
-  fn<<<(a.nq + wpb - 1) / wpb, wpb * 32, smem, (cudaStream_t)stream>>>(a);
+  const int grid = launch_grid(fn, a, wpb, smem);
+  int c = start_counter(a, (cudaStream_t)stream);
+  if (c) return c;
+  fn<<<grid, wpb * 32, smem, (cudaStream_t)stream>>>(a);
   return (int)cudaGetLastError();
 }
 
@@ -789,7 +837,10 @@ int launch_search_sparse(const SearchArgs& a, const SparseArgs& sp, int wpb, voi
   const size_t smem = (size_t)wpb * a.warp_smem;
   cudaError_t e = cudaFuncSetAttribute(search_sparse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return (int)e;
-  search_sparse_kernel<<<(a.nq + wpb - 1) / wpb, wpb * 32, smem, (cudaStream_t)stream>>>(a, sp);
+  const int grid = launch_grid(search_sparse_kernel, a, wpb, smem);
+  int c = start_counter(a, (cudaStream_t)stream);
+  if (c) return c;
+  search_sparse_kernel<<<grid, wpb * 32, smem, (cudaStream_t)stream>>>(a, sp);
   return (int)cudaGetLastError();
 }
 

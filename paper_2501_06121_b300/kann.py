@@ -59,8 +59,9 @@ class kann_sparse_desc(ctypes.Structure):
 
 class kann_search_opts(ctypes.Structure):
     _fields_ = [("rerank", ctypes.c_int32), ("max_hops", ctypes.c_int32), ("hash_bits", ctypes.c_int32),
-                ("warps_per_block", ctypes.c_int32), ("lanes_per_row", ctypes.c_int32), ("reserved", ctypes.c_int32),
-                ("d_status", ctypes.c_void_p), ("d_counters", ctypes.c_void_p)]
+                ("warps_per_block", ctypes.c_int32), ("lanes_per_row", ctypes.c_int32), ("prefetch", ctypes.c_int32),
+                ("d_status", ctypes.c_void_p), ("d_counters", ctypes.c_void_p),
+                ("d_work_counter", ctypes.c_void_p), ("d_n", ctypes.c_void_p)]
 
 
 _L = None
@@ -87,6 +88,9 @@ def _lib():
             "kann_hnsw_levels": (I, [I64, I, U64, P, P, P]),
             "kann_hnsw_build_dense": (I, [P, I64, I, I, I, I, U64, I, P, P, P, P, P]),
             "kann_hnsw_build_sparse": (I, [P, P, P, I64, I, I, U64, I, P, P, P, P, P]),
+            "kann_pq_train_workspace_bytes": (SZ, [I, I]),
+            "kann_pq_train": (I, [P, I64, I, I, I, U64, P, P, SZ, P]),
+            "kann_pq_encode": (I, [P, I64, I, I, P, P, P]),
             "kann_status_str": (ctypes.c_char_p, [I]),
             "kann_last_cuda_error": (I, []),
         }
@@ -123,12 +127,15 @@ def _require_cuda(*ts):
 class Index:
     """A kann_index_t plus the device tensors it borrows (kept alive here)."""
 
-    def __init__(self, handle, keep, kind, d, metric):
+    def __init__(self, handle, keep, kind, d, metric, dtype=None, n=0, M0=0):
         self.handle = handle
         self._keep = keep
         self.kind = kind
         self.d = d
         self.metric = metric
+        self.dtype = dtype
+        self.n = n
+        self.M0 = M0
 
     def __del__(self):
         if getattr(self, "handle", None) is not None and _L is not None:
@@ -191,14 +198,17 @@ def kann_index_upload(graph, vectors=None, dtype=KANN_F32, metric=KANN_L2, scale
     ref = lambda s: ctypes.byref(s) if s is not None else None
     _check("kann_index_upload", _lib().kann_index_upload(ctypes.byref(h), ctypes.byref(gd), ref(vd), ref(pd), ref(sd),
                                                          ref(rd), int(bool(validate_ids))))
-    return Index(h, keep, kind, d, metric)
+    return Index(h, keep, kind, d, metric, dtype=dtype if kind == "dense" else kind, n=int(graph["n"]),
+                 M0=int(graph["M0"]))
 
 
-def _opts(rerank=0, max_hops=0, hash_bits=0, warps_per_block=0, lanes_per_row=0, status=None, counters=None):
-    _require_cuda(status, counters)
-    return kann_search_opts(int(rerank), int(max_hops), int(hash_bits), int(warps_per_block), int(lanes_per_row), 0,
-                            status.data_ptr() if status is not None else None,
-                            counters.data_ptr() if counters is not None else None)
+def _opts(rerank=0, max_hops=0, hash_bits=0, warps_per_block=0, lanes_per_row=0, status=None, counters=None,
+          work_counter=None, n_device=None, prefetch=0):
+    _require_cuda(status, counters, work_counter, n_device)
+    p = lambda t: t.data_ptr() if t is not None else None
+    return kann_search_opts(int(rerank), int(max_hops), int(hash_bits), int(warps_per_block), int(lanes_per_row),
+                            int(prefetch),
+                            p(status), p(counters), p(work_counter), p(n_device))
 
 
 def kann_search(index, queries, k, ef, ids=None, dists=None, stream=None):
@@ -207,7 +217,9 @@ def kann_search(index, queries, k, ef, ids=None, dists=None, stream=None):
 
 def kann_search_ex(index, queries, k, ef, ids=None, dists=None, stream=None, **opts):
     """queries [n, d] float32 on the device -> (ids [n, k] int32, dists [n, k] float32).
-    opts: rerank, max_hops, hash_bits, warps_per_block, lanes_per_row, status ([n] int32
+    opts: rerank, max_hops, hash_bits, warps_per_block, lanes_per_row, work_counter ([1] int32
+    tensor: persistent work-stealing launch), n_device ([1] int32: device-side query count,
+    persistent mode), status ([n] int32
     tensor, bits KANN_QSTAT_*), counters ([n, 4] int32 tensor)."""
     _require_cuda(queries)
     n = queries.shape[0]
@@ -283,6 +295,28 @@ def kann_quantize(x, dtype, stream=None):
     scale = torch.empty(n, dtype=torch.float32, device=x.device) if dtype == KANN_E4M3 else None
     _check("kann_quantize", _lib().kann_quantize(_dev(x), n, d, dtype, _dev(out), _dev(scale), _stream(stream)))
     return out, scale
+
+
+def kann_pq_train(x, m, iters=25, seed=0, stream=None):
+    """Device PQ codebooks [m, 256, d/m] float32 trained on FP32 rows x [n, d]."""
+    _require_cuda(x)
+    n, d = x.shape
+    cb = torch.empty((m, 256, d // m), dtype=torch.float32, device=x.device)
+    wsb = int(_lib().kann_pq_train_workspace_bytes(d, m))
+    ws = torch.empty(max(wsb, 16), dtype=torch.uint8, device=x.device)
+    _check("kann_pq_train", _lib().kann_pq_train(_dev(x), n, d, m, iters, seed, _dev(cb), _dev(ws), ws.numel(),
+                                                 _stream(stream)))
+    return cb
+
+
+def kann_pq_encode(x, codebooks, stream=None):
+    """uint8 codes [n, m] of FP32 rows x [n, d] for device codebooks [m, 256, dsub]."""
+    _require_cuda(x, codebooks)
+    n, d = x.shape
+    m = codebooks.shape[0]
+    codes = torch.empty((n, m), dtype=torch.uint8, device=x.device)
+    _check("kann_pq_encode", _lib().kann_pq_encode(_dev(x), n, d, m, _dev(codebooks), _dev(codes), _stream(stream)))
+    return codes
 
 
 # --------------------------------------------------------------------------- host graph build

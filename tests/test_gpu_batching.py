@@ -1,0 +1,117 @@
+"""Batching and serving patterns: the persistent work-stealing launch, CUDA
+graph replay with a device-side batch size, and the continuous-batching
+server.  A query's result depends only on the query, its k and ef: the same
+bits alone, in a mixed batch, in any launch form, and in the server's mix."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from paper_2501_06121_b300 import datagen as G
+from paper_2501_06121_b300 import kann as K
+from paper_2501_06121_b300 import serving as S
+
+pytestmark = pytest.mark.gpu
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.fixture(scope="module")
+def two_indices(cfg1_small):
+    X, Q, g = cfg1_small
+    Xd = dev(X)
+    idx_a = K.kann_index_upload(K.graph_to_device(g.arrays()), vectors=Xd)
+    # second index: E4M3 traversal + FP32 re-rank over a different data set
+    X2, Q2 = G.gaussian_mixture(8000, 300, d=64, clusters=16, sigma=3.0, seed=77)
+    g2 = O.build_dense(X2, O.L2, 16, 100, 77)
+    X2d = dev(X2)
+    c8, s8 = K.kann_quantize(X2d, K.KANN_E4M3)
+    idx_b = K.kann_index_upload(K.graph_to_device(g2.arrays()), vectors=c8, dtype=K.KANN_E4M3, scale=s8, rerank=X2d)
+    return dict(a=(idx_a, Q, Xd), b=(idx_b, Q2, (X2d, c8, s8)))
+
+
+def single(idx, q, k, ef, **o):
+    ids, d = K.kann_search_ex(idx, dev(q[None]), k, ef, **o)
+    torch.cuda.synchronize()
+    return ids.cpu().numpy()[0], d.cpu().numpy()[0]
+
+
+def test_persistent_equals_plain(two_indices):
+    idx, Q, _ = two_indices["a"]
+    rng = np.random.default_rng(1)
+    n = 700
+    ks = rng.choice([10, 100], n).astype(np.int32)
+    efs = rng.integers(64, 513, n).astype(np.int32)
+    a_i, a_d = K.kann_search_batch(idx, dev(Q[:n]), dev(ks), dev(efs), kmax=100, efmax=512)
+    ctr = torch.zeros(1, dtype=torch.int32, device="cuda")
+    b_i, b_d = K.kann_search_batch(idx, dev(Q[:n]), dev(ks), dev(efs), kmax=100, efmax=512, work_counter=ctr)
+    torch.cuda.synchronize()
+    assert torch.equal(a_i, b_i) and torch.equal(a_d, b_d)
+    assert int(ctr.item()) >= n
+
+
+def test_device_side_count_and_graph_replay(two_indices):
+    idx, Q, _ = two_indices["a"]
+    cap, kmax, efmax = 256, 10, 128
+    q = torch.zeros((cap, 128), device="cuda")
+    k = torch.full((cap,), 10, dtype=torch.int32, device="cuda")
+    ef = torch.full((cap,), 64, dtype=torch.int32, device="cuda")
+    n = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ctr = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ids = torch.full((cap, kmax), -7, dtype=torch.int32, device="cuda")
+    dd = torch.zeros((cap, kmax), device="cuda")
+    s = torch.cuda.Stream()
+    launch = lambda: K.kann_search_batch(idx, q, k, ef, kmax=kmax, efmax=efmax, ids=ids, dists=dd, stream=s,
+                                         work_counter=ctr, n_device=n)
+    with torch.cuda.stream(s):
+        launch()
+    s.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s, capture_error_mode="relaxed"):
+        launch()
+    for rep, nn in enumerate((37, 256, 1)):
+        ids.fill_(-7)
+        q.copy_(dev(Q[rep * 256:rep * 256 + cap]))
+        n.fill_(nn)
+        torch.cuda.synchronize()
+        with torch.cuda.stream(s):
+            g.replay()
+        s.synchronize()
+        ref_i, ref_d = K.kann_search_ex(idx, q[:nn], 10, 64)
+        torch.cuda.synchronize()
+        assert torch.equal(ids[:nn], ref_i) and torch.equal(dd[:nn], ref_d)
+        assert bool((ids[nn:] == -7).all())  # rows past the device-side count are untouched
+
+
+def test_server_results_equal_alone_and_in_the_mix(two_indices):
+    idx_a, Qa, _ = two_indices["a"]
+    idx_b, Qb, _ = two_indices["b"]
+    indices = {"a": dict(index=idx_a, d=128, kmax=100, efmax=512),
+               "b": dict(index=idx_b, d=64, kmax=100, efmax=512, opts=dict(rerank=-1))}
+    srv = S.SearchServer(indices, slots_per_index=3, slot_capacity=128)
+    reqs = S.poisson_requests(20000.0, 0.05, {"a": Qa, "b": Qb}, seed=5)
+    done = srv.run(reqs, time_limit=30.0)
+    assert len(done) == len(reqs)
+    for r in done[::7]:
+        idx = idx_a if r["index"] == "a" else idx_b
+        o = dict(rerank=-1) if r["index"] == "b" else {}
+        si, sd = single(idx, r["query"], r["k"], r["ef"], **o)
+        assert np.array_equal(si, r["ids"]) and np.array_equal(sd, r["dists"])
+    summ = S.latency_summary(done, 0.05)
+    assert summ["completed"] == len(reqs) and summ["p99_ms"] >= summ["p50_ms"] > 0
+
+
+def test_autotuner_returns_result_preserving_settings(two_indices, tmp_path):
+    from paper_2501_06121_b300 import autotune as A
+    idx, Q, _ = two_indices["a"]
+    Qd = dev(Q[:500])
+    cache = str(tmp_path / "tune.json")
+    opts = A.tune(idx, Qd, 10, 64, reps=2, cache_path=cache)
+    assert set(opts) == {"lanes_per_row", "hash_bits", "warps_per_block", "prefetch", "persistent"}
+    a_i, a_d = A.search_with(idx, Qd, 10, 64, opts)
+    b_i, b_d = K.kann_search_ex(idx, Qd, 10, 64)
+    torch.cuda.synchronize()
+    assert torch.equal(a_i, b_i) and torch.equal(a_d, b_d)
+    assert A.tune(idx, Qd, 10, 64, reps=2, cache_path=cache) == opts  # served from the cache

@@ -190,6 +190,43 @@ def run_reference(args):
     print(json.dumps(out))
 
 
+def run_serving(g, Xd, Q, dev, args):
+    """Continuous-batching serving: two resident indices (this 1M x 128 set and
+    a 10k x 128 Gaussian-mixture set), both with E4M3 per-vector-scaled
+    traversal + FP32 re-rank; Poisson arrivals at each rate, k in {10, 100},
+    ef uniform in 64..512; latency = completion seen on the host - arrival."""
+    from paper_2501_06121_b300 import datagen as G
+    from paper_2501_06121_b300 import kann as K_
+    from paper_2501_06121_b300 import serving as S
+    c8, s8 = K_.kann_quantize(Xd, K_.KANN_E4M3)
+    big = K_.kann_index_upload(K_.graph_to_device(g, dev), vectors=c8, dtype=K_.KANN_E4M3, scale=s8,
+                               metric=K_.KANN_L2, rerank=Xd)
+    X1, Q1 = G.gaussian_mixture(10000, 1000, d=128, clusters=32, sigma=5.0, seed=1)
+    g1 = K_.kann_hnsw_build_dense(X1, K_.KANN_L2, 16, 100, 1, nthreads=0)
+    X1d = torch_from(X1, dev)
+    c1, s1 = K_.kann_quantize(X1d, K_.KANN_E4M3)
+    small = K_.kann_index_upload(K_.graph_to_device(g1, dev), vectors=c1, dtype=K_.KANN_E4M3, scale=s1,
+                                 metric=K_.KANN_L2, rerank=X1d)
+    spec = dict(kmax=100, efmax=512, opts=dict(rerank=-1))
+    srv = S.SearchServer({"1Mx128": dict(spec, index=big, d=128), "10kx128": dict(spec, index=small, d=128)},
+                         slots_per_index=3, slot_capacity=2048, memory_budget=256 << 20)
+    out = {"indices": "1M x 128 integer mixture + 10k x 128 Gaussian mixture, E4M3 traversal + FP32 re-rank (R = ef)",
+           "k": [10, 100], "ef": [64, 512], "seconds_per_rate": args.serving_seconds,
+           "slot_device_bytes": srv.device_bytes, "rates": []}
+    for i, rate in enumerate(float(r) for r in args.serving_rates.split(",")):
+        reqs = S.poisson_requests(rate, args.serving_seconds, {"1Mx128": Q, "10kx128": Q1}, seed=100 + i)
+        done = srv.run(reqs, time_limit=args.serving_seconds * 3 + 5)
+        summ = S.latency_summary(done, max(r["t_done"] for r in done) if done else 1.0)
+        summ.update(offered_qps=rate, requests=len(reqs))
+        out["rates"].append(summ)
+    return out
+
+
+def torch_from(a, dev):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+
+
 def traffic_from_profiles(kernel_sha):
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
@@ -210,6 +247,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ef", type=int, default=0, help="fix ef instead of sweeping")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-seconds", type=float, default=2.0)
+    ap.add_argument("--serving-rates", default="5000,20000,50000,100000,200000")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -363,6 +403,10 @@ def main():
     e2e_qps = world * N_QUERY * args.steps / (e2e_ms / 1e3)
     final_recall = recall_at(ids_buf.cpu().numpy(), gt)
 
+    serving = None
+    if rank == 0 and world == 1 and not args.no_serving:
+        serving = run_serving(g, Xd, Q, dev, args)
+
     cpu_base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu_base = cpu_oracle_qps(g, X, Q, ef)
@@ -393,6 +437,7 @@ def main():
             "gpu_launches": args.steps,
             "clocks": clk,
             "cpu_baseline": cpu_base,
+            "serving": serving,
         }
         print(json.dumps(out))
     if world > 1:

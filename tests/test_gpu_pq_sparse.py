@@ -134,3 +134,27 @@ def test_sparse_long_query_is_flagged(sparse_setup):
     torch.cuda.synchronize()
     assert (st.cpu().numpy()[0] & K.KANN_QSTAT_QUERY_TRUNCATED) != 0
     assert np.all(gi.cpu().numpy() >= 0)
+
+
+def test_device_pq_encode_matches_oracle_on_integer_data():
+    # integer data and codebooks: every FP32 distance is exact, so the nearest
+    # centroid (ties to the lowest index) is the same decision on both sides
+    rng = np.random.default_rng(9)
+    X = rng.integers(0, 16, (3000, 64)).astype(np.float32)
+    cb = rng.integers(0, 16, (16, 256, 4)).astype(np.float32)
+    codes = K.kann_pq_encode(dev(X), dev(cb))
+    torch.cuda.synchronize()
+    assert np.array_equal(codes.cpu().numpy(), O.pq_encode(X, cb))
+
+
+def test_device_pq_training_reduces_error():
+    X, _ = G.vmf_mixture(20000, 1, d=64, clusters=16, kappa=50.0, seed=61)
+    Xd = dev(X)
+    cb0 = K.kann_pq_train(Xd, 16, iters=0, seed=3)
+    cb = K.kann_pq_train(Xd, 16, iters=15, seed=3)
+    torch.cuda.synchronize()
+    err = lambda c: float(np.mean((O.pq_reconstruct(O.pq_encode(X, c.cpu().numpy()), c.cpu().numpy()) - X) ** 2))
+    e0, e1 = err(cb0), err(cb)
+    _, obj = O.pq_train(X[:5000], m=16, ksub=256, iters=15, seed=3)
+    assert e1 < 0.8 * e0
+    assert e1 < 1.5 * float(obj[:, -1].mean() / 4)  # per-dimension MSE near the oracle's k-means

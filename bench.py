@@ -227,6 +227,128 @@ def torch_from(a, dev):
     return torch.from_numpy(np.ascontiguousarray(a)).to(dev)
 
 
+def run_pq768(args, n=None, concentration=None):
+    """The MS MARCO-shaped workload: 1M x 768 unit-norm vMF mixture (1,024
+    directions, kappa 50), 10k queries, inner product, HNSW M=32 efC=200 on
+    the FP32 vectors, PQ m=192 x 256 trained on the GPU on a 100k sample;
+    ADC traversal with an exact FP32 re-rank of the best 100, k = 10 and 100;
+    the plain FP32 traversal beside it.  Ground truth: exact FP32 k-NN."""
+    import torch
+    from paper_2501_06121_b300 import build as lib_build
+    from paper_2501_06121_b300 import datagen as G
+    from paper_2501_06121_b300 import kann as K_
+    lib_build.build()
+    dev = torch.device("cuda", 0)
+    n = n or args.pq_n
+    concentration = concentration if concentration is not None else args.pq_concentration
+    t0 = time.time()
+    X, Q = G.vmf_mixture(n, 10_000, d=768, clusters=1024, kappa=50.0, seed=3,
+                         concentration=concentration if concentration > 0 else None)
+    gen_s = time.time() - t0
+    key = "pq768-%d-%g" % (X.shape[0], concentration)
+    path = os.path.join(tempfile.gettempdir(), "kann_bench_graph_%s.npz" % key)
+    t0 = time.time()
+    if os.path.exists(path):
+        z = np.load(path)
+        g = {k: (z[k] if z[k].ndim else int(z[k])) for k in z.files}
+    else:
+        g = K_.kann_hnsw_build_dense(X, K_.KANN_IP, 32, 200, 3, nthreads=0)
+        np.savez(path + ".tmp.npz", **g)
+        os.replace(path + ".tmp.npz", path)
+    build_s = time.time() - t0
+    Xd = torch.from_numpy(X).to(dev)
+    Qd = torch.from_numpy(Q).to(dev)
+    del X
+    cb = K_.kann_pq_train(Xd[:min(n, 100_000)].contiguous(), 192, iters=25, seed=3)
+    codes = K_.kann_pq_encode(Xd, cb)
+    gd = K_.graph_to_device(g, dev)
+    idx_pq = K_.kann_index_upload(gd, pq=dict(codes=codes, codebooks=cb, metric=K_.KANN_IP), rerank=Xd)
+    idx32 = K_.kann_index_upload(gd, vectors=Xd, dtype=K_.KANN_F32, metric=K_.KANN_IP)
+    t0 = time.time()
+    gt100, _ = K_.kann_exact_knn(Qd, Xd, 100, K_.KANN_IP)
+    torch.cuda.synchronize()
+    gt_s = time.time() - t0
+    gt100 = gt100.cpu().numpy()
+
+    def timed(fn, reps=5):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+        e0.record()
+        for _ in range(reps):
+            out = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps, out
+
+    rows = []
+    for k in (10, 100):
+        for ef in (128, 256, 512, 1024):
+            if ef < k:
+                continue
+            ms, (ids, _) = timed(lambda: K_.kann_search_ex(idx_pq, Qd, k, ef, rerank=100 if k <= 100 else -1))
+            r = recall_at(ids.cpu().numpy(), gt100, k)
+            ms32, (ids32, _) = timed(lambda: K_.kann_search_ex(idx32, Qd, k, ef))
+            r32 = recall_at(ids32.cpu().numpy(), gt100, k)
+            rows.append({"k": k, "ef": ef, "pq_rerank100_qps": 1e4 / (ms / 1e3), "pq_rerank100_recall": r,
+                         "fp32_qps": 1e4 / (ms32 / 1e3), "fp32_recall": r32})
+            print(json.dumps(rows[-1]), flush=True)
+    out = {"workload": "pq768", "n": n, "concentration": concentration,
+           "metric": "QPS and recall@k over ef, n x 768 IP, PQ m=192 + FP32 re-rank of 100 vs plain FP32",
+           "data_gen_s": gen_s, "graph_build_s": build_s,
+           "ground_truth_s": gt_s, "rows": rows}
+    print(json.dumps(out))
+
+
+def run_sparse(args, n_docs=100_000):
+    """The Splade-shaped workload at reduced size: 100k documents over a
+    30,522-term vocabulary (nnz ~ Poisson(120), Zipf(1.1) terms, lognormal
+    weights), 10k queries (nnz ~ Poisson(40)), inner product, HNSW M=32
+    efC=200 built on the host; QPS over all queries, recall@10 against the
+    GPU sparse brute force on the first 1,000 queries."""
+    import torch
+    from paper_2501_06121_b300 import build as lib_build
+    from paper_2501_06121_b300 import datagen as G
+    from paper_2501_06121_b300 import kann as K_
+    lib_build.build()
+    dev = torch.device("cuda", 0)
+    t0 = time.time()
+    base, qs = G.sparse_zipf(n_docs, 10_000, vocab=30522, lam_doc=120, lam_query=40, seed=4)
+    gen_s = time.time() - t0
+    t0 = time.time()
+    g = K_.kann_hnsw_build_sparse(base, 32, 200, 4, nthreads=0)
+    build_s = time.time() - t0
+    td = lambda c: (torch.from_numpy(c[0]).to(dev), torch.from_numpy(c[1].view(np.int16)).to(dev),
+                    torch.from_numpy(c[2]).to(dev))
+    b_d, q_d = td(base), td(qs)
+    idx = K_.kann_index_upload(K_.graph_to_device(g, dev), sparse=dict(indptr=b_d[0], terms=b_d[1], weights=b_d[2],
+                                                                        vocab=30522))
+    ngt = 1000
+    q_gt = td((qs[0][:ngt + 1], qs[1][:qs[0][ngt]], qs[2][:qs[0][ngt]]))
+    t0 = time.time()
+    gt, _ = K_.kann_exact_knn_sparse(b_d, q_gt, 30522, 10)
+    torch.cuda.synchronize()
+    gt_s = time.time() - t0
+    gt = gt.cpu().numpy()
+    rows = []
+    for ef in (32, 64, 128, 256, 512, 1024):
+        run = lambda: K_.kann_search_sparse(idx, q_d[0], q_d[1], q_d[2], 10, ef)
+        run()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+        e0.record()
+        for _ in range(5):
+            ids, _ = run()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 5
+        rows.append({"ef": ef, "qps": 1e4 / (ms / 1e3), "ms": ms,
+                     "recall@10": recall_at(ids.cpu().numpy()[:ngt], gt, 10)})
+        print(json.dumps(rows[-1]), flush=True)
+    print(json.dumps({"workload": "sparse100k", "docs": n_docs, "data_gen_s": gen_s, "graph_build_s": build_s,
+                      "ground_truth_s_1000q": gt_s, "rows": rows}))
+
+
 def traffic_from_profiles(kernel_sha):
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
@@ -250,9 +372,17 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serving-seconds", type=float, default=2.0)
     ap.add_argument("--serving-rates", default="5000,20000,50000,100000,200000")
+    ap.add_argument("--workload", default="sift1m", choices=["sift1m", "pq768", "sparse100k"])
+    ap.add_argument("--pq-n", type=int, default=1_000_000)
+    ap.add_argument("--pq-concentration", type=float, default=0.0,
+                    help="> 0: normalize(mu + sigma g) mixture instead of the kappa=50 vMF draw")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "pq768":
+        return run_pq768(args)
+    if args.workload == "sparse100k":
+        return run_sparse(args)
 
     import torch
     import torch.distributed as dist
@@ -322,9 +452,6 @@ def main():
                    + DIM * 4 + K * 8)
 
     stream = torch.cuda.current_stream()
-
-    def step(index, rr):
-        return K_.kann_search_ex(index, Qd, K, ef, rerank=rr)
 
     ids_buf = torch.empty((N_QUERY, K), dtype=torch.int32, device=dev)
     d_buf = torch.empty((N_QUERY, K), dtype=torch.float32, device=dev)

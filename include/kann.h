@@ -129,8 +129,8 @@ typedef struct kann_index kann_index_t;
  * the dataset holds the items and their encoding, the index decides which
  * items a query is compared with).  Exactly one traversal source
  * must be given: `v` (dense), `pq`, or `sp`.  `rerank` (nullable) is a dense
- * KANN_F32 copy of the same items with the same d and metric, used for exact
- * re-ranking of reduced-precision traversal.  The graph's metadata and
+ * KANN_F32 (exact) or KANN_BF16 copy of the same items with the same d and
+ * metric, used to re-rank the traversal's best candidates.  The graph's metadata and
  * degree caps are validated on the host; with `validate_ids` != 0 the
  * adjacency arrays are also scanned on the device for ids outside [0, n)
  * (one synchronising call).  On success *out owns a host record only.
@@ -146,15 +146,16 @@ int kann_index_destroy(kann_index_t* idx);
 /* Optional search settings (zero-initialise, then set what is needed). */
 typedef struct {
   int32_t rerank;          /* 0: no re-rank; R > 0: re-rank the best min(R, |W|) traversal
-                              candidates exactly in FP32 from the index's rerank copy;
+                              candidates from the index's rerank copy (FP32 arithmetic);
                               -1: R = ef_eff.  R must be >= k. */
   int32_t max_hops;        /* cap on layer-0 expansions per query; 0 = 1,000,000 */
   int32_t hash_bits;       /* log2 of the per-query visited table; 0 = automatic */
   int32_t warps_per_block; /* queries per CTA (one warp each); 0 = automatic */
   int32_t lanes_per_row;   /* lanes sharing one row gather (power of two <= 32); 0 = automatic */
-  int32_t prefetch;        /* 1 = L2-prefetch the adjacency row of every entry that enters W;
-                              0 = automatic (off: measured no gain on the 1M x 128 workload);
-                              -1 = off */
+  int32_t lean;            /* dense rows of <= 2 chunks per lane: 1 = half the row batches in
+                              flight for a 64-register budget (more warps per SM), -1 = off,
+                              0 = automatic (off) */
+  int32_t reserved;
   uint32_t* d_status;      /* [n] per-query KANN_QSTAT_* bits, nullable */
   int32_t* d_counters;     /* [n][4] per-query counters, nullable: layer-0 distance
                               evaluations, layer-0 expansions, upper-layer distance
@@ -207,6 +208,16 @@ int kann_exact_knn(const void* d_queries, const void* d_base, int nq, int64_t nb
                    int k, int32_t* d_ids, float* d_dists, void* d_ws, size_t ws_bytes, void* stream);
 
 size_t kann_exact_knn_workspace_bytes(int nq, int64_t nb, int d, int k, int dtype);
+
+/* Exact k-NN for sparse inner product (ground truth of the sparse measure):
+ * base CSR (d_indptr [nb+1], d_terms, d_weights) and query CSR (d_q_indptr
+ * [nq+1], d_q_terms, d_q_weights), term ids < vocab (vocab * 4 bytes plus
+ * 16 KB must fit one CTA's shared memory: vocab <= ~50k).  Distance = -IP in
+ * FP32; d_ids / d_dists [nq][k] sorted by (distance, id); k <= 128.  Cost is
+ * one full pass over the base per query: meant for sampled ground truth. */
+int kann_exact_knn_sparse(const int64_t* d_indptr, const uint16_t* d_terms, const float* d_weights, int64_t nb,
+                          const int64_t* d_q_indptr, const uint16_t* d_q_terms, const float* d_q_weights, int nq,
+                          int vocab, int k, int32_t* d_ids, float* d_dists, void* stream);
 
 /* kann_exact_knn_noalloc: the same exact k-NN, for callers that cannot
  * allocate device memory -- for example code running inside a host

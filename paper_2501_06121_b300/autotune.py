@@ -39,7 +39,7 @@ def _time(index, Q, k, ef, reps, opts):
 
 def tune(index, queries, k, ef, rerank=0, reps=5, cache_path=None, verbose=False):
     """Returns the fastest result-preserving option dict for kann_search_ex
-    (keys lanes_per_row, hash_bits, warps_per_block, prefetch, persistent)."""
+    (keys lanes_per_row, hash_bits, warps_per_block, lean, persistent)."""
     key = _signature(index, k, ef, rerank)
     cache = {}
     if cache_path and os.path.exists(cache_path):
@@ -48,7 +48,7 @@ def tune(index, queries, k, ef, rerank=0, reps=5, cache_path=None, verbose=False
         if key in cache:
             return dict(cache[key]["opts"])
     base_t, (ref_i, ref_d) = _time(index, queries, k, ef, reps, dict(rerank=rerank))
-    best, best_t = dict(lanes_per_row=0, hash_bits=0, warps_per_block=0, prefetch=0, persistent=False), base_t
+    best, best_t = dict(lanes_per_row=0, hash_bits=0, warps_per_block=0, lean=0, persistent=False), base_t
     results = []
 
     def trial(o):
@@ -64,11 +64,11 @@ def tune(index, queries, k, ef, rerank=0, reps=5, cache_path=None, verbose=False
 
     for lpr in (0, 2, 4, 8, 16, 32):
         for hb in (0, 9, 10, 11, 12):
-            trial(dict(lanes_per_row=lpr, hash_bits=hb, warps_per_block=0, prefetch=0, persistent=False))
+            trial(dict(lanes_per_row=lpr, hash_bits=hb, warps_per_block=0, lean=0, persistent=False))
     for wpb in (1, 2, 4):
         for pers in (False, True):
             trial(dict(best, warps_per_block=wpb, persistent=pers))
-    trial(dict(best, prefetch=1))
+    trial(dict(best, lean=1))
     if verbose:
         for o, t, same in sorted(results, key=lambda r: r[1])[:10]:
             print("%8.3f ms  same=%s  %s" % (t, same, o))

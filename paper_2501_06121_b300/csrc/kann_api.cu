@@ -142,7 +142,6 @@ int fill_search_args(const kann_index_t* idx, const float* d_q, int n, int k, in
   a.out_ids = d_ids;
   a.out_d = d_dists;
   a.max_hops = 1000000;
-  a.prefetch = 0;
   int hbits = 0;
   wpb = 4;
   int R = 0;
@@ -158,8 +157,8 @@ int fill_search_args(const kann_index_t* idx, const float* d_q, int n, int k, in
     const int l = opts->lanes_per_row;
     if (l < 0 || l > 32 || (l & (l - 1)) != 0) return KANN_EINVAL;
     a.lpr_override = l;
-    if (opts->prefetch < -1 || opts->prefetch > 1) return KANN_EINVAL;
-    a.prefetch = opts->prefetch > 0 ? 1 : 0;
+    if (opts->lean < -1 || opts->lean > 1) return KANN_EINVAL;
+    a.lean = opts->lean > 0 ? 1 : 0;
     R = opts->rerank;
     if (R < -1) return KANN_EINVAL;
     a.work_counter = opts->d_work_counter;
@@ -172,9 +171,11 @@ int fill_search_args(const kann_index_t* idx, const float* d_q, int n, int k, in
     a.R = R;
     a.rr_data = (const unsigned char*)idx->rr.d_data;
     a.rr_stride = idx->rr.row_stride_bytes;
-    a.rr_nchunks = idx->rr.d / 4;
-    // the mapping an FP32 traversal of the same rows uses by default
-    a.rr_lpr = lanes_per_row(a.rr_nchunks, default_chunks_per_lane(KANN_F32));
+    a.rr_dtype = idx->rr.dtype;
+    a.rr_nchunks = idx->rr.d * elem_size(idx->rr.dtype) / 16;
+    // the mapping a traversal of the same rows uses by default (bit-identical
+    // distances to an FP32 traversal when the copy is FP32)
+    a.rr_lpr = lanes_per_row(a.rr_nchunks, default_chunks_per_lane(idx->rr.dtype));
   }
   a.hbits = hbits ? hbits : default_hbits(a.efmax);
   int efcap = 32;
@@ -194,6 +195,7 @@ int run_dense(const kann_index_t* idx, SearchArgs& a, int wpb, void* stream) {
   a.lpr = a.lpr_override ? a.lpr_override : lanes_per_row(a.nchunks, default_chunks_per_lane(v.dtype));
   if (a.lpr > a.nchunks && a.nchunks >= 1) a.lpr = lanes_per_row(a.nchunks);
   if ((a.nchunks + a.lpr - 1) / a.lpr > 8) return KANN_EINVAL;
+  if ((a.nchunks + a.lpr - 1) / a.lpr > 2) a.lean = 0;  // the lean form exists for <= 2 chunks per lane
   if (a.nq > 0 && (!a.q || !aligned16(a.q))) return KANN_EINVAL;
   a.warp_smem = search_warp_smem(a.efcap, a.hbits);
   const int optin = max_optin_smem();
@@ -327,7 +329,7 @@ int kann_index_upload(kann_index_t** out, const kann_graph_desc* g, const kann_v
     if (!sp->d_indptr || !sp->d_terms || !sp->d_weights || sp->vocab < 1 || sp->vocab > 65536) rc = KANN_EINVAL;
   }
   if (rc == KANN_OK && rerank) {
-    if (rerank->dtype != KANN_F32) rc = KANN_EINVAL;
+    if (rerank->dtype != KANN_F32 && rerank->dtype != KANN_BF16) rc = KANN_EINVAL;
     else rc = validate_vectors(rerank, g->n);
     if (rc == KANN_OK && idx->kind == 0 && (rerank->d != v->d || rerank->metric != v->metric)) rc = KANN_EINVAL;
     if (rc == KANN_OK && idx->kind == 1 && (rerank->d != pq->m * pq->dsub || rerank->metric != pq->metric))

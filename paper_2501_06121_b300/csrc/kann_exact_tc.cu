@@ -7,7 +7,7 @@
 // are never written to HBM.
 //
 // One persistent CTA per SM walks work items (a tile of 128 queries x one
-// split of the base).  Roles inside a CTA (192 threads):
+// split of the base).  Roles inside a CTA (320 threads):
 //   warp 0      TMA producer: per base tile of 256 rows and per 64-element K
 //               chunk, loads the query chunk (128 x 64) and the base chunk
 //               (256 x 64), 128-byte swizzled, into a 4-stage ring;
@@ -15,9 +15,11 @@
 //               and issues tcgen05.mma (M=128, N=256, K=16) from one lane;
 //               tcgen05.commit frees a ring stage when its MMAs are done and
 //               signals a full accumulator;
-//   warps 2..5  epilogue warpgroup: thread r owns query row r (TMEM lane r),
-//               reads its 256 scores with tcgen05.ld, filters them against its
-//               current k-th distance and inserts the survivors.
+//   warps 2..9  two epilogue warpgroups: thread r of group g owns query row r
+//               (TMEM lane r) over columns [128 g, 128 g + 128) of each tile,
+//               reads its scores with tcgen05.ld into registers, filters them
+//               against its current k-th distance and inserts the survivors
+//               into its own top-k list in shared memory.
 // Accumulators are double-buffered so the epilogue of tile t overlaps the
 // MMAs of tile t+1.  Every mbarrier wait is bounded by a %globaltimer
 // deadline; on expiry the CTA raises an error flag and all roles wind down,
@@ -36,13 +38,14 @@ namespace {
 constexpr int TC_M = 128;       // queries per work item (TMEM lanes)
 constexpr int TC_N = 256;       // base rows per tile (accumulator columns)
 constexpr int TC_K = 64;        // K elements per stage: one 128-byte swizzle row
-constexpr int TC_STAGES = 4;
+constexpr int TC_MAX_STAGES = 4;
 constexpr int A_BYTES = TC_M * TC_K * 2;
 constexpr int B_BYTES = TC_N * TC_K * 2;
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-constexpr int TC_THREADS = 192;
+constexpr int TC_EPI_WARPS = 8;     // two warpgroups, one per half of a tile's columns
+constexpr int TC_THREADS = 64 + 32 * TC_EPI_WARPS;
 constexpr uint32_t TMEM_COLS = 512;
-constexpr int TC_KMAX = 32;     // largest k kept in registers by the epilogue
+constexpr int TC_KMAX = 32;     // largest k of the tensor-core path (top-k lists in shared memory)
 constexpr unsigned long long WAIT_NS = 2000000000ull;  // 2 s per wait
 
 struct TcArgs {
@@ -51,6 +54,7 @@ struct TcArgs {
   int d, metric, k, S, kchunks;
   int64_t per;          // base rows per split (a multiple of TC_N)
   int n_items;
+  int stages;           // ring depth (3 or 4, by shared memory left for the top-k lists)
   uint32_t idesc;
   const float* xnorm;   // [nb]
   const float* qnorm;   // [nq]
@@ -189,30 +193,58 @@ __device__ __forceinline__ void tc_ld64(uint32_t taddr, float* v) {
   for (int i = 0; i < 64; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// A thread's top-k list lives in shared memory (its own k slots); the
+// registers hold the current worst entry's distance and slot.
+struct TopkWorst {
+  float thr;
+  int slot;
+};
+
+// Put (dist, col) in the worst slot and find the new worst by (d, id).
+__device__ __noinline__ TopkWorst topk_insert(float* ld, int* li, int k, int slot, float dist, int col) {
+  ld[slot] = dist;
+  li[slot] = col;
+  float wd = -__int_as_float(0x7f800000);
+  int wid = -2, wi = 0;
+  for (int m = 0; m < k; ++m) {
+    const float d = ld[m];
+    const int id = li[m];
+    if (d > wd || (d == wd && id > wid)) {
+      wd = d;
+      wid = id;
+      wi = m;
+    }
+  }
+  return TopkWorst{wd, wi};
+}
+
 // ---- the kernel ------------------------------------------------------------
 __global__ void __launch_bounds__(TC_THREADS, 1)
     exact_tc_kernel(const __grid_constant__ CUtensorMap tmQ, const __grid_constant__ CUtensorMap tmX, const TcArgs a) {
   extern __shared__ unsigned char smem_raw[];
   // 1024-byte alignment for the swizzled stages
   unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int NS = a.stages;
   unsigned char* stage_base = smem;
-  u64* bars = reinterpret_cast<u64*>(smem + TC_STAGES * STAGE_BYTES);
-  // bars: full[STAGES], empty[STAGES], tfull[2], tempty[2]
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * TC_STAGES + 4);
-  float* xn_s = reinterpret_cast<float*>(tmem_slot + 4);  // [4][TC_N] per-warp tile norms
+  u64* bars = reinterpret_cast<u64*>(smem + NS * STAGE_BYTES);
+  // bars: full[NS], empty[NS], tfull[2], tempty[2]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * TC_MAX_STAGES + 4);
+  float* xn_s = reinterpret_cast<float*>(tmem_slot + 4);        // [8][128] per-warp tile norms
+  float* list_d = xn_s + TC_EPI_WARPS * 128;                    // [2][128][k] top-k distances
+  int* list_i = reinterpret_cast<int*>(list_d + 2 * TC_M * a.k); // [2][128][k] top-k ids
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + TC_STAGES);
-  const uint32_t tfull0 = smem_u32(bars + 2 * TC_STAGES), tempty0 = smem_u32(bars + 2 * TC_STAGES + 2);
+  const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + TC_MAX_STAGES);
+  const uint32_t tfull0 = smem_u32(bars + 2 * TC_MAX_STAGES), tempty0 = smem_u32(bars + 2 * TC_MAX_STAGES + 2);
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < TC_STAGES; ++s) {
+    for (int s = 0; s < NS; ++s) {
       mbar_init(full0 + 8 * s, 1);
       mbar_init(empty0 + 8 * s, 1);
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(tfull0 + 8 * b, 1);
-      mbar_init(tempty0 + 8 * b, 4);
+      mbar_init(tempty0 + 8 * b, TC_EPI_WARPS);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -238,7 +270,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         const int64_t b_end = b_begin + a.per < a.nb ? b_begin + a.per : a.nb;
         for (int64_t b0 = b_begin; b0 < b_end && ok; b0 += TC_N) {
           for (int kc = 0; kc < a.kchunks && ok; ++kc, ++it) {
-            const uint32_t s = it % TC_STAGES, ph = (it / TC_STAGES) & 1u;
+            const uint32_t s = it % NS, ph = (it / NS) & 1u;
             ok = mbar_wait(empty0 + 8 * s, ph ^ 1u, a.err);
             if (!ok) break;
             const uint32_t sa = smem_u32(stage_base + s * STAGE_BYTES);
@@ -264,7 +296,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           tc_fence_after();
           const uint32_t dt = tmem + buf * TC_N;
           for (int kc = 0; kc < a.kchunks; ++kc, ++it) {
-            const uint32_t s = it % TC_STAGES, ph = (it / TC_STAGES) & 1u;
+            const uint32_t s = it % NS, ph = (it / NS) & 1u;
             ok = mbar_wait(full0 + 8 * s, ph, a.err);
             if (!ok) break;
             tc_fence_after();
@@ -280,10 +312,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       }
     }
   } else {
-    // ---------------- epilogue warpgroup ----------------
+    // ---------------- epilogue warpgroups ----------------
     const int quarter = warp & 3;            // TMEM lanes 32*quarter .. +31
     const int row = quarter * 32 + lane;
-    float* xw = xn_s + (warp - 2) * TC_N;    // this warp's copy of the tile's norms
+    const int grp = (warp - 2) >> 2;         // column half of each tile
+    float* xw = xn_s + (warp - 2) * 128;     // this warp's copy of its columns' norms
+    float* ld = list_d + ((size_t)grp * TC_M + row) * a.k;
+    int* li = list_i + ((size_t)grp * TC_M + row) * a.k;
     uint32_t t = 0;
     bool ok = true;
     for (int item = blockIdx.x; item < a.n_items && ok; item += gridDim.x) {
@@ -291,51 +326,49 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       const int split = item % a.S;
       const int64_t b_begin = (int64_t)split * a.per;
       const int64_t b_end = b_begin + a.per < a.nb ? b_begin + a.per : a.nb;
-      float kd[TC_KMAX];
-      int ki[TC_KMAX];
-#pragma unroll
-      for (int j = 0; j < TC_KMAX; ++j) {
-        kd[j] = j < a.k ? __int_as_float(0x7f800000) : -__int_as_float(0x7f800000);
-        ki[j] = -1;
+      for (int j = 0; j < a.k; ++j) {
+        ld[j] = __int_as_float(0x7f800000);
+        li[j] = -1;
       }
-      float thr = __int_as_float(0x7f800000);
-      int worst = 0;
+      TopkWorst w{__int_as_float(0x7f800000), 0};
       for (int64_t b0 = b_begin; b0 < b_end; b0 += TC_N, ++t) {
         const uint32_t buf = t & 1u, use = t >> 1;
+        const int64_t c_base = b0 + grp * 128;
         if (a.metric == KANN_L2)
-          for (int j = lane; j < TC_N; j += 32) xw[j] = (b0 + j < b_end) ? __ldg(a.xnorm + b0 + j) : 0.f;
+          for (int j = lane; j < 128; j += 32) xw[j] = (c_base + j < b_end) ? __ldg(a.xnorm + c_base + j) : 0.f;
         __syncwarp();
         ok = mbar_wait_warp(tfull0 + 8 * buf, use & 1u, a.err, lane);
         if (!ok) break;
         tc_fence_after();
-        for (int c0 = 0; c0 < TC_N; c0 += 64) {
+#pragma unroll 1
+        for (int c0 = 0; c0 < 128; c0 += 64) {
           float v[64];
-          tc_ld64(tmem + ((uint32_t)(quarter * 32) << 16) + buf * TC_N + c0, v);
-#pragma unroll 4
-          for (int j = 0; j < 64; ++j) {
-            const int64_t col = b0 + c0 + j;
-            const float dist = a.metric == KANN_L2 ? fmaf(-2.f, v[j], xw[c0 + j]) : -v[j];
-            if (dist < thr && col < b_end) {
-              // replace the worst entry, then find the new worst by (d, id);
-              // columns arrive in increasing id order, so a tie never enters
+          tc_ld64(tmem + ((uint32_t)(quarter * 32) << 16) + buf * TC_N + grp * 128 + c0, v);
+          const int64_t cb = c_base + c0;
+          // pass 1: distances and a mask of those that beat the current k-th
+          uint32_t m0 = 0u, m1 = 0u;
 #pragma unroll
-              for (int m = 0; m < TC_KMAX; ++m)
-                if (m == worst) {
-                  kd[m] = dist;
-                  ki[m] = (int)col;
-                }
-              float wd = -__int_as_float(0x7f800000);
-              int wid = -2, wi = 0;
+          for (int j = 0; j < 64; j += 4) {
+            float4 n4 = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (a.metric == KANN_L2) n4 = *reinterpret_cast<const float4*>(xw + c0 + j);
+            const float nn[4] = {n4.x, n4.y, n4.z, n4.w};
 #pragma unroll
-              for (int m = 0; m < TC_KMAX; ++m) {
-                if (m < a.k && (kd[m] > wd || (kd[m] == wd && ki[m] > wid))) {
-                  wd = kd[m];
-                  wid = ki[m];
-                  wi = m;
-                }
-              }
-              thr = wd;
-              worst = wi;
+            for (int u = 0; u < 4; ++u) {
+              v[j + u] = a.metric == KANN_L2 ? fmaf(-2.f, v[j + u], nn[u]) : -v[j + u];
+              const uint32_t bit = v[j + u] < w.thr ? 1u : 0u;
+              if (j + u < 32) m0 |= bit << (j + u);
+              else m1 |= bit << (j + u - 32);
+            }
+          }
+          // pass 2 (rare once the list is full): insert in column order;
+          // columns arrive in increasing id order, so a tie never enters
+          if (m0 | m1) {
+            const bool tail = cb + 64 > b_end;
+#pragma unroll
+            for (int j = 0; j < 64; ++j) {
+              const bool bit = ((j < 32 ? m0 >> j : m1 >> (j - 32)) & 1u) != 0u;
+              if (bit && v[j] < w.thr && (!tail || cb + j < b_end))
+                w = topk_insert(ld, li, a.k, w.slot, v[j], (int)(cb + j));
             }
           }
         }
@@ -346,11 +379,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       if (!ok) break;
       if (q < a.nq) {
         const float qn = a.metric == KANN_L2 ? a.qnorm[q] : 0.f;
-        u64* o = a.out + ((size_t)q * a.S + split) * a.k;
-#pragma unroll
-        for (int j = 0; j < TC_KMAX; ++j)
-          if (j < a.k) o[j] = ki[j] < 0 ? ((u64)ordered_bits(__int_as_float(0x7f800000)) << 32) | 0xffffffffull
-                                        : make_key(kd[j] + qn, (uint32_t)ki[j]);
+        u64* o = a.out + (((size_t)q * a.S + split) * 2 + grp) * a.k;
+        for (int j = 0; j < a.k; ++j)
+          o[j] = li[j] < 0 ? ((u64)ordered_bits(__int_as_float(0x7f800000)) << 32) | 0xffffffffull
+                           : make_key(ld[j] + qn, (uint32_t)li[j]);
       }
     }
   }
@@ -465,7 +497,7 @@ size_t exact_tc_workspace_bytes(int nq, int64_t nb, int k) {
   int S;
   int64_t per;
   exact_tc_plan(nq, nb, &S, &per);
-  return (size_t)nq * S * k * 8 + (size_t)nb * 4 + (size_t)nq * 4 + 256;
+  return (size_t)nq * S * 2 * k * 8 + (size_t)nb * 4 + (size_t)nq * 4 + 256;
 }
 
 bool exact_tc_supported(int dtype, int d, int k) {
@@ -479,7 +511,7 @@ int exact_tc_run(const void* Q, const void* X, int nq, int64_t nb, int d, int me
   exact_tc_plan(nq, nb, &S, &per);
   unsigned char* w = static_cast<unsigned char*>(ws);
   u64* part = reinterpret_cast<u64*>(w);
-  float* xn = reinterpret_cast<float*>(w + (size_t)nq * S * k * 8);
+  float* xn = reinterpret_cast<float*>(w + (size_t)nq * S * 2 * k * 8);
   float* qn = xn + nb;
   int* err = reinterpret_cast<int*>(((uintptr_t)(qn + nq) + 15) & ~(uintptr_t)15);
   CUtensorMap mq, mx;
@@ -505,7 +537,14 @@ int exact_tc_run(const void* Q, const void* X, int nq, int64_t nb, int d, int me
   a.qnorm = qn;
   a.out = part;
   a.err = err;
-  const size_t smem = 1024 + (size_t)TC_STAGES * STAGE_BYTES + (2 * TC_STAGES + 4) * 8 + 16 + 4 * TC_N * 4;
+  // shared memory: alignment pad, stage ring, barriers, norms, top-k lists
+  const size_t fixed = 1024 + (2 * TC_MAX_STAGES + 4) * 8 + 16 + TC_EPI_WARPS * 128 * 4 + (size_t)2 * TC_M * k * 8;
+  int optin = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  a.stages = TC_MAX_STAGES;
+  while (a.stages > 2 && fixed + (size_t)a.stages * STAGE_BYTES > (size_t)optin) --a.stages;
+  const size_t smem = fixed + (size_t)a.stages * STAGE_BYTES;
   e = cudaFuncSetAttribute(exact_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return (int)e;
   const int grid = a.n_items < num_sms() ? a.n_items : num_sms();
@@ -513,13 +552,13 @@ int exact_tc_run(const void* Q, const void* X, int nq, int64_t nb, int d, int me
   e = cudaGetLastError();
   if (e != cudaSuccess) return (int)e;
   int P = 32;
-  while (P < S * k) P <<= 1;
+  while (P < 2 * S * k) P <<= 1;
   int wpb = 4;
   while (wpb > 1 && (size_t)wpb * P * 8 > 160 * 1024) wpb >>= 1;
   const size_t msmem = (size_t)wpb * P * 8;
   e = cudaFuncSetAttribute(exact_tc_merge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msmem);
   if (e != cudaSuccess) return (int)e;
-  exact_tc_merge_kernel<<<(nq + wpb - 1) / wpb, wpb * 32, msmem, s>>>(part, err, nq, S, k, P, ids, dists);
+  exact_tc_merge_kernel<<<(nq + wpb - 1) / wpb, wpb * 32, msmem, s>>>(part, err, nq, 2 * S, k, P, ids, dists);
   return (int)cudaGetLastError();
 }
 

@@ -30,6 +30,7 @@ struct SearchArgs {
   const unsigned char* rr_data;
   int64_t rr_stride;
   int rr_nchunks, rr_lpr, R;
+  int rr_dtype;        // KANN_F32 or KANN_BF16
   // queries and outputs
   const float* q;
   int nq, k, ef, kmax, efmax;
@@ -43,7 +44,7 @@ struct SearchArgs {
   int lpr_override;  // 0 = automatic lanes per row
   int* work_counter;     // persistent mode: next query index (zeroed before launch), or null
   const int32_t* d_n;    // persistent mode: device-side query count (<= nq), or null
-  int prefetch;          // L2-prefetch the adjacency rows of new W entries
+  int lean;              // dense: half the rows in flight, 64-register budget
   int efcap;       // W capacity (power of two >= efmax, >= 32)
   int warp_smem;   // bytes of shared memory per warp
 };

@@ -58,11 +58,6 @@ __device__ __forceinline__ int visit(uint32_t* H, int hbits, uint32_t id) {
   return 2;
 }
 
-// Bulk prefetch of `bytes` (a multiple of 16, 16-byte aligned) into L2.
-__device__ __forceinline__ void prefetch_l2(const void* p, int bytes) {
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
-}
-
 __device__ __forceinline__ int lower_bound_w(const u64* W, int len, u64 key) {
   int lo = 0, hi = len;
   while (lo < hi) {
@@ -92,10 +87,11 @@ __device__ __forceinline__ int count_le(const int* A, int n, int x) {
 // in flight per warp.  The summation order of a row's distance depends only
 // on the row, never on its slot in the batch.
 // ---------------------------------------------------------------------------
-template <int DT, int CPL>
+template <int DT, int CPL, bool LEAN = false>
 struct DenseBackend {
   static constexpr int EPC = Fmt<DT>::EPC;
-  static constexpr int U = (8 / CPL) > 0 ? (8 / CPL) : 1;
+  // row batches in flight: 32 buffer registers per lane, 16 in the lean form
+  static constexpr int U = ((LEAN ? 4 : 8) / CPL) > 0 ? ((LEAN ? 4 : 8) / CPL) : 1;
   float qr[CPL][EPC];
 
   __device__ __forceinline__ void init(const SearchArgs& a, int qi, int lane, unsigned char*) {
@@ -321,9 +317,11 @@ struct SparseBackend {
 // lane/chunk mapping and summation order as the FP32 dense back-end (chunks
 // in order, elements in order, then the butterfly), so a re-ranked distance
 // is bit-identical to the FP32 traversal distance of the same row.
+template <int RDT>
 __device__ __forceinline__ void rerank_dists(const unsigned char* rr, int64_t stride, int nchunks, int lpr, int metric,
                                              const float* q, const int* cid, int cnt, u64* ck, int lane) {
   constexpr int U = 4;
+  constexpr int EPC = Fmt<RDT>::EPC;
   const int rpi = 32 / lpr;
   const int sub = lane & (lpr - 1), grp = lane / lpr;
   const int cpl = (nchunks + lpr - 1) / lpr;
@@ -338,8 +336,16 @@ __device__ __forceinline__ void rerank_dists(const unsigned char* rr, int64_t st
     }
     for (int c = 0; c < cpl; ++c) {
       const int ch = sub + c * lpr;
-      const float4 qv =
-          ch < nchunks ? __ldg(reinterpret_cast<const float4*>(q) + ch) : make_float4(0.f, 0.f, 0.f, 0.f);
+      float qq[EPC];
+#pragma unroll
+      for (int e4 = 0; e4 < EPC / 4; ++e4) {
+        const float4 qv = ch < nchunks ? __ldg(reinterpret_cast<const float4*>(q + ch * EPC) + e4)
+                                       : make_float4(0.f, 0.f, 0.f, 0.f);
+        qq[4 * e4] = qv.x;
+        qq[4 * e4 + 1] = qv.y;
+        qq[4 * e4 + 2] = qv.z;
+        qq[4 * e4 + 3] = qv.w;
+      }
       uint4 buf[U];
 #pragma unroll
       for (int u = 0; u < U; ++u)
@@ -347,11 +353,10 @@ __device__ __forceinline__ void rerank_dists(const unsigned char* rr, int64_t st
                                                : make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
       for (int u = 0; u < U; ++u) {
-        const float x[4] = {__uint_as_float(buf[u].x), __uint_as_float(buf[u].y), __uint_as_float(buf[u].z),
-                            __uint_as_float(buf[u].w)};
-        const float qq[4] = {qv.x, qv.y, qv.z, qv.w};
+        float x[EPC];
+        Fmt<RDT>::unpack(buf[u], x);
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
+        for (int e = 0; e < EPC; ++e) {
           if (metric == KANN_L2) {
             const float t = qq[e] - x[e];
             acc[u] = fmaf(t, t, acc[u]);
@@ -373,13 +378,14 @@ __device__ __forceinline__ void rerank_dists(const unsigned char* rr, int64_t st
 
 // Re-rank the best R entries of W exactly and sort them (cold path, once per
 // query).  Returns the number of re-ranked entries now at the front of W.
-__device__ __noinline__ int rerank_phase(const unsigned char* rr, int64_t stride, int nchunks, int lpr, int metric,
-                                         const float* q, int R, u64* W, u64* ck, int* cid, int lane) {
+__device__ __noinline__ int rerank_phase(const unsigned char* rr, int rr_dtype, int64_t stride, int nchunks, int lpr,
+                                         int metric, const float* q, int R, u64* W, u64* ck, int* cid, int lane) {
   for (int b = 0; b < R; b += 64) {
     const int cb = min(64, R - b);
     for (int j = lane; j < cb; j += 32) cid[j] = (int)key_id(W[b + j]);
     __syncwarp();
-    rerank_dists(rr, stride, nchunks, lpr, metric, q, cid, cb, ck, lane);
+    if (rr_dtype == KANN_BF16) rerank_dists<KANN_BF16>(rr, stride, nchunks, lpr, metric, q, cid, cb, ck, lane);
+    else rerank_dists<KANN_F32>(rr, stride, nchunks, lpr, metric, q, cid, cb, ck, lane);
     __syncwarp();
     for (int j = lane; j < cb; j += 32) W[b + j] = ck[j];
     __syncwarp();
@@ -639,12 +645,7 @@ __device__ __forceinline__ void search_one(const SearchArgs& a, B& be, int qi, i
         }
         for (int j = lane; j < cnew; j += 32) {
           const int pos = j + clb[j];
-          if (pos < ef) {
-            W[pos] = ck[j];
-            // a new entry of W is likely to be expanded soon: start pulling its
-            // adjacency row into L2 now, so that expansion waits on L2, not DRAM
-            if (a.prefetch) prefetch_l2(a.l0 + (int64_t)key_id(ck[j]) * a.M0, a.M0 * 4);
-          }
+          if (pos < ef) W[pos] = ck[j];
         }
         __syncwarp();
         len = min(len + cnew, ef);
@@ -663,7 +664,7 @@ __device__ __forceinline__ void search_one(const SearchArgs& a, B& be, int qi, i
   int nout = len;
   if (a.R != 0 && a.rr_data != nullptr) {
     const int R = min(a.R < 0 ? ef : a.R, len);
-    nout = rerank_phase(a.rr_data, a.rr_stride, a.rr_nchunks, a.rr_lpr, a.metric, a.q + (size_t)qi * a.d, R, W, ck,
+    nout = rerank_phase(a.rr_data, a.rr_dtype, a.rr_stride, a.rr_nchunks, a.rr_lpr, a.metric, a.q + (size_t)qi * a.d, R, W, ck,
                         cid, lane);
   }
 
@@ -693,11 +694,12 @@ __device__ __forceinline__ void search_one(const SearchArgs& a, B& be, int qi, i
 }
 
 // Register budget from the query registers a lane holds: <= 8 -> 64
-// registers (32 warps per SM), <= 16 -> 80 (24 warps), wider -> 128.
-template <int DT, int CPLT>
+// registers (32 warps per SM), <= 16 -> 80 (24 warps), wider -> 128.  The
+// lean form (half the rows in flight) always asks for 64 when q <= 16.
+template <int DT, int CPLT, bool LEAN>
 struct MinBlocks {
   static constexpr int q = CPLT * Fmt<DT>::EPC;
-  static constexpr int value = q <= 8 ? 8 : (q <= 16 ? 6 : 4);
+  static constexpr int value = q <= 8 ? 8 : (q <= 16 ? (LEAN ? 8 : 6) : 4);
 };
 
 // Queries of one launch: a plain grid gives warp w of CTA b query
@@ -725,9 +727,9 @@ __device__ __forceinline__ void run_queries(const SearchArgs& a, B& be) {
   }
 }
 
-template <int DT, int CPLT>
-__global__ void __launch_bounds__(128, MinBlocks<DT, CPLT>::value) search_dense_kernel(const SearchArgs a) {
-  DenseBackend<DT, CPLT> be;
+template <int DT, int CPLT, bool LEAN>
+__global__ void __launch_bounds__(128, MinBlocks<DT, CPLT, LEAN>::value) search_dense_kernel(const SearchArgs a) {
+  DenseBackend<DT, CPLT, LEAN> be;
   run_queries(a, be);
 }
 
@@ -746,12 +748,14 @@ __global__ void __launch_bounds__(128, 4) search_sparse_kernel(const SearchArgs 
 typedef void (*KernelFn)(const SearchArgs);
 
 template <int DT>
-KernelFn pick_dense(int cplt) {
-  switch (cplt) {
-    case 1: return search_dense_kernel<DT, 1>;
-    case 2: return search_dense_kernel<DT, 2>;
-    case 4: return search_dense_kernel<DT, 4>;
-    case 8: return search_dense_kernel<DT, 8>;
+KernelFn pick_dense(int cplt, bool lean) {
+  switch (cplt * 2 + (lean ? 1 : 0)) {
+    case 2: return search_dense_kernel<DT, 1, false>;
+    case 3: return search_dense_kernel<DT, 1, true>;
+    case 4: return search_dense_kernel<DT, 2, false>;
+    case 5: return search_dense_kernel<DT, 2, true>;
+    case 8: return search_dense_kernel<DT, 4, false>;
+    case 16: return search_dense_kernel<DT, 8, false>;
     default: return nullptr;
   }
 }
@@ -793,10 +797,10 @@ int launch_search_dense(const SearchArgs& a, int dtype, int wpb, void* stream) {
   const int cplt = pow2_at_least((a.nchunks + a.lpr - 1) / a.lpr);
   KernelFn fn = nullptr;
   switch (dtype) {
-    case KANN_F32: fn = pick_dense<KANN_F32>(cplt); break;
-    case KANN_F16: fn = pick_dense<KANN_F16>(cplt); break;
-    case KANN_BF16: fn = pick_dense<KANN_BF16>(cplt); break;
-    case KANN_E4M3: fn = pick_dense<KANN_E4M3>(cplt); break;
+    case KANN_F32: fn = pick_dense<KANN_F32>(cplt, a.lean); break;
+    case KANN_F16: fn = pick_dense<KANN_F16>(cplt, a.lean); break;
+    case KANN_BF16: fn = pick_dense<KANN_BF16>(cplt, a.lean); break;
+    case KANN_E4M3: fn = pick_dense<KANN_E4M3>(cplt, a.lean); break;
     default: break;
   }
   if (!fn) return (int)cudaErrorInvalidValue;

@@ -59,7 +59,8 @@ class kann_sparse_desc(ctypes.Structure):
 
 class kann_search_opts(ctypes.Structure):
     _fields_ = [("rerank", ctypes.c_int32), ("max_hops", ctypes.c_int32), ("hash_bits", ctypes.c_int32),
-                ("warps_per_block", ctypes.c_int32), ("lanes_per_row", ctypes.c_int32), ("prefetch", ctypes.c_int32),
+                ("warps_per_block", ctypes.c_int32), ("lanes_per_row", ctypes.c_int32), ("lean", ctypes.c_int32),
+                ("reserved", ctypes.c_int32),
                 ("d_status", ctypes.c_void_p), ("d_counters", ctypes.c_void_p),
                 ("d_work_counter", ctypes.c_void_p), ("d_n", ctypes.c_void_p)]
 
@@ -88,6 +89,7 @@ def _lib():
             "kann_hnsw_levels": (I, [I64, I, U64, P, P, P]),
             "kann_hnsw_build_dense": (I, [P, I64, I, I, I, I, U64, I, P, P, P, P, P]),
             "kann_hnsw_build_sparse": (I, [P, P, P, I64, I, I, U64, I, P, P, P, P, P]),
+            "kann_exact_knn_sparse": (I, [P, P, P, I64, P, P, P, I, I, I, P, P, P]),
             "kann_pq_train_workspace_bytes": (SZ, [I, I]),
             "kann_pq_train": (I, [P, I64, I, I, I, U64, P, P, SZ, P]),
             "kann_pq_encode": (I, [P, I64, I, I, P, P, P]),
@@ -165,7 +167,7 @@ def kann_index_upload(graph, vectors=None, dtype=KANN_F32, metric=KANN_L2, scale
     `dtype` (uint8 codes for KANN_E4M3 with `scale` [n] float32).
     pq: dict(codes=[n, m] uint8, codebooks=[m, 256, dsub] float32, metric).
     sparse: dict(indptr, terms (int16 view of uint16), weights, vocab).
-    rerank: [n, d] float32 device tensor (exact re-rank copy)."""
+    rerank: [n, d] float32 (exact) or bfloat16 device tensor (re-rank copy)."""
     gd = kann_graph_desc(graph["n"], graph["M"], graph["M0"], graph["max_level"], graph["entry"],
                          graph["n_upper"], graph["level"].data_ptr(), graph["l0"].data_ptr(),
                          graph["upper_slot"].data_ptr(), graph["upper"].data_ptr())
@@ -192,7 +194,7 @@ def kann_index_upload(graph, vectors=None, dtype=KANN_F32, metric=KANN_L2, scale
         kind, d = "sparse", None
         metric = KANN_IP
     if rerank is not None:
-        rd = _vec_desc(rerank, KANN_F32, metric)
+        rd = _vec_desc(rerank, KANN_BF16 if rerank.dtype == torch.bfloat16 else KANN_F32, metric)
         keep.append(rerank)
     h = ctypes.c_void_p()
     ref = lambda s: ctypes.byref(s) if s is not None else None
@@ -203,11 +205,11 @@ def kann_index_upload(graph, vectors=None, dtype=KANN_F32, metric=KANN_L2, scale
 
 
 def _opts(rerank=0, max_hops=0, hash_bits=0, warps_per_block=0, lanes_per_row=0, status=None, counters=None,
-          work_counter=None, n_device=None, prefetch=0):
+          work_counter=None, n_device=None, lean=0):
     _require_cuda(status, counters, work_counter, n_device)
     p = lambda t: t.data_ptr() if t is not None else None
     return kann_search_opts(int(rerank), int(max_hops), int(hash_bits), int(warps_per_block), int(lanes_per_row),
-                            int(prefetch),
+                            int(lean), 0,
                             p(status), p(counters), p(work_counter), p(n_device))
 
 
@@ -284,6 +286,22 @@ def kann_exact_knn(queries, base, k, metric, dtype=KANN_F32, ws=None, ids=None, 
     _check("kann_exact_knn", _lib().kann_exact_knn(_dev(queries), _dev(base), nq, nb, d, metric, dtype, k, _dev(ids),
                                                    _dev(dists), _dev(ws), ws.numel() * ws.element_size(),
                                                    _stream(stream)))
+    return ids, dists
+
+
+def kann_exact_knn_sparse(base, queries, vocab, k, ids=None, dists=None, stream=None):
+    """Sparse-IP brute force: base / queries are (indptr int64, terms int16-view
+    of uint16, weights float32) device CSR triples."""
+    _require_cuda(*base, *queries)
+    nq = queries[0].shape[0] - 1
+    dev = queries[0].device
+    if ids is None:
+        ids = torch.empty((nq, k), dtype=torch.int32, device=dev)
+    if dists is None:
+        dists = torch.empty((nq, k), dtype=torch.float32, device=dev)
+    _check("kann_exact_knn_sparse", _lib().kann_exact_knn_sparse(
+        _dev(base[0]), _dev(base[1]), _dev(base[2]), base[0].shape[0] - 1, _dev(queries[0]), _dev(queries[1]),
+        _dev(queries[2]), nq, vocab, k, _dev(ids), _dev(dists), _stream(stream)))
     return ids, dists
 
 

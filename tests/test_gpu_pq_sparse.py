@@ -158,3 +158,19 @@ def test_device_pq_training_reduces_error():
     _, obj = O.pq_train(X[:5000], m=16, ksub=256, iters=15, seed=3)
     assert e1 < 0.8 * e0
     assert e1 < 1.5 * float(obj[:, -1].mean() / 4)  # per-dimension MSE near the oracle's k-means
+
+
+def test_sparse_exact_knn_matches_oracle():
+    base, qs = G.sparse_zipf(5000, 200, vocab=3000, lam_doc=40, lam_query=12, seed=71)
+    td = lambda c: (dev(c[0]), dev(c[1].view(np.int16)), dev(c[2]))
+    gi, gd = K.kann_exact_knn_sparse(td(base), td(qs), 3000, 20)
+    torch.cuda.synchronize()
+    gi, gd = gi.cpu().numpy(), gd.cpu().numpy()
+    oi, od = O.exact_sparse(base, qs, 20)
+    assert id_set_match_fraction(gi, oi) >= 0.99
+    Xd = G.densify(base, 3000).astype(np.float64)
+    Qd = G.densify(qs, 3000).astype(np.float64)
+    ref = -np.einsum("qd,qkd->qk", Qd, Xd[gi])
+    mag = np.einsum("qd,qkd->qk", np.abs(Qd), np.abs(Xd[gi]))
+    assert np.all(np.abs(gd - ref) <= 1e-5 * np.maximum(np.abs(ref), mag) + 1e-30)
+    assert np.all(np.diff(gd, axis=1) >= 0)

@@ -305,3 +305,19 @@ def test_exact_knn_integer_exact(int_small):
     gi, gd = K.kann_exact_knn(dev(Q), dev(X), 20, K.KANN_L2)
     torch.cuda.synchronize()
     assert np.array_equal(gi.cpu().numpy(), ei) and np.array_equal(gd.cpu().numpy().astype(np.float64), ed)
+
+
+
+def test_bf16_rerank_copy(cfg1_small):
+    X, Q, g = cfg1_small
+    Xd = dev(X)
+    Xb, _ = K.kann_quantize(Xd, K.KANN_BF16)
+    Xh, _ = K.kann_quantize(Xd, K.KANN_F16)
+    idx = K.kann_index_upload(K.graph_to_device(g.arrays()), vectors=Xh, dtype=K.KANN_F16, rerank=Xb)
+    gi, gd = search(idx, Q, 10, 64, rerank=-1)
+    th = Xh.cpu().view(torch.int16).numpy().view(np.uint16)
+    tb = Xb.cpu().view(torch.int16).numpy().view(np.uint16)
+    ti, _, _ = O.search_dense(g, th, Q, 64, 64, O.L2, dtype=O.DT_F16)
+    oi, od = O.rerank_dense(tb, Q, ti, 10, O.L2, dtype=O.DT_BF16)
+    assert id_set_match_fraction(gi, oi) >= 0.999
+    check_dists(tb, Q, gi, gd, O.L2, dtype=O.DT_BF16)

@@ -152,7 +152,7 @@ typedef struct {
   int32_t hash_bits;       /* log2 of the per-query visited table; 0 = automatic */
   int32_t warps_per_block; /* queries per CTA (one warp each); 0 = automatic */
   int32_t lanes_per_row;   /* lanes sharing one row gather (power of two <= 32); 0 = automatic */
-  int32_t lean;            /* dense rows of <= 2 chunks per lane: 1 = half the row batches in
+  int32_t lean;            /* dense rows of 2 chunks per lane: 1 = half the row batches in
                               flight for a 64-register budget (more warps per SM), -1 = off,
                               0 = automatic (off) */
   int32_t reserved;

@@ -195,7 +195,7 @@ int run_dense(const kann_index_t* idx, SearchArgs& a, int wpb, void* stream) {
   a.lpr = a.lpr_override ? a.lpr_override : lanes_per_row(a.nchunks, default_chunks_per_lane(v.dtype));
   if (a.lpr > a.nchunks && a.nchunks >= 1) a.lpr = lanes_per_row(a.nchunks);
   if ((a.nchunks + a.lpr - 1) / a.lpr > 8) return KANN_EINVAL;
-  if ((a.nchunks + a.lpr - 1) / a.lpr > 2) a.lean = 0;  // the lean form exists for <= 2 chunks per lane
+  if ((a.nchunks + a.lpr - 1) / a.lpr != 2) a.lean = 0;  // the lean form exists for 2 chunks per lane
   if (a.nq > 0 && (!a.q || !aligned16(a.q))) return KANN_EINVAL;
   a.warp_smem = search_warp_smem(a.efcap, a.hbits);
   const int optin = max_optin_smem();

@@ -87,7 +87,7 @@ __device__ __forceinline__ int count_le(const int* A, int n, int x) {
 // in flight per warp.  The summation order of a row's distance depends only
 // on the row, never on its slot in the batch.
 // ---------------------------------------------------------------------------
-template <int DT, int CPL, bool LEAN = false>
+template <int DT, int CPL, bool LEAN = false, int MET = KANN_L2>
 struct DenseBackend {
   static constexpr int EPC = Fmt<DT>::EPC;
   // row batches in flight: 32 buffer registers per lane, 16 in the lean form
@@ -142,7 +142,7 @@ struct DenseBackend {
 #pragma unroll
           for (int e = 0; e < EPC; ++e) {
             const float xv = (DT == KANN_E4M3) ? x[e] * sc[u] : x[e];
-            if (a.metric == KANN_L2) {
+            if (MET == KANN_L2) {
               const float t = qr[c][e] - xv;
               acc = fmaf(t, t, acc);
             } else {
@@ -151,7 +151,7 @@ struct DenseBackend {
           }
         }
         for (int o = lpr >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
-        if (sub == 0 && r < cnt) ck[r] = make_key(a.metric == KANN_L2 ? acc : -acc, (uint32_t)cid[r]);
+        if (sub == 0 && r < cnt) ck[r] = make_key(MET == KANN_L2 ? acc : -acc, (uint32_t)cid[r]);
       }
     }
   }
@@ -727,9 +727,9 @@ __device__ __forceinline__ void run_queries(const SearchArgs& a, B& be) {
   }
 }
 
-template <int DT, int CPLT, bool LEAN>
+template <int DT, int CPLT, bool LEAN, int MET>
 __global__ void __launch_bounds__(128, MinBlocks<DT, CPLT, LEAN>::value) search_dense_kernel(const SearchArgs a) {
-  DenseBackend<DT, CPLT, LEAN> be;
+  DenseBackend<DT, CPLT, LEAN, MET> be;
   run_queries(a, be);
 }
 
@@ -747,17 +747,21 @@ __global__ void __launch_bounds__(128, 4) search_sparse_kernel(const SearchArgs 
 
 typedef void (*KernelFn)(const SearchArgs);
 
-template <int DT>
-KernelFn pick_dense(int cplt, bool lean) {
+template <int DT, int MET>
+KernelFn pick_dense_m(int cplt, bool lean) {
   switch (cplt * 2 + (lean ? 1 : 0)) {
-    case 2: return search_dense_kernel<DT, 1, false>;
-    case 3: return search_dense_kernel<DT, 1, true>;
-    case 4: return search_dense_kernel<DT, 2, false>;
-    case 5: return search_dense_kernel<DT, 2, true>;
-    case 8: return search_dense_kernel<DT, 4, false>;
-    case 16: return search_dense_kernel<DT, 8, false>;
+    case 2: return search_dense_kernel<DT, 1, false, MET>;
+    case 4: return search_dense_kernel<DT, 2, false, MET>;
+    case 5: return search_dense_kernel<DT, 2, true, MET>;
+    case 8: return search_dense_kernel<DT, 4, false, MET>;
+    case 16: return search_dense_kernel<DT, 8, false, MET>;
     default: return nullptr;
   }
+}
+
+template <int DT>
+KernelFn pick_dense(int cplt, bool lean, int metric) {
+  return metric == KANN_L2 ? pick_dense_m<DT, KANN_L2>(cplt, lean) : pick_dense_m<DT, KANN_IP>(cplt, lean);
 }
 
 // Grid of a launch: one warp per query, or (persistent) as many CTAs as fit
@@ -797,10 +801,10 @@ int launch_search_dense(const SearchArgs& a, int dtype, int wpb, void* stream) {
   const int cplt = pow2_at_least((a.nchunks + a.lpr - 1) / a.lpr);
   KernelFn fn = nullptr;
   switch (dtype) {
-    case KANN_F32: fn = pick_dense<KANN_F32>(cplt, a.lean); break;
-    case KANN_F16: fn = pick_dense<KANN_F16>(cplt, a.lean); break;
-    case KANN_BF16: fn = pick_dense<KANN_BF16>(cplt, a.lean); break;
-    case KANN_E4M3: fn = pick_dense<KANN_E4M3>(cplt, a.lean); break;
+    case KANN_F32: fn = pick_dense<KANN_F32>(cplt, a.lean, a.metric); break;
+    case KANN_F16: fn = pick_dense<KANN_F16>(cplt, a.lean, a.metric); break;
+    case KANN_BF16: fn = pick_dense<KANN_BF16>(cplt, a.lean, a.metric); break;
+    case KANN_E4M3: fn = pick_dense<KANN_E4M3>(cplt, a.lean, a.metric); break;
     default: break;
   }
   if (!fn) return (int)cudaErrorInvalidValue;

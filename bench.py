@@ -349,6 +349,19 @@ def run_sparse(args, n_docs=100_000):
                       "ground_truth_s_1000q": gt_s, "rows": rows}))
 
 
+SEARCH_KERNEL_SOURCES = ("kann_device.cuh", "kann_internal.h", "kann_search_impl.cuh", "kann_search_f16.cu")
+
+
+def search_kernel_sha():
+    """SHA-1 over the sources of the FP16 dense search kernel, to tie stored
+    DRAM counters to the kernel they were captured from."""
+    h = hashlib.sha1()
+    for name in SEARCH_KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2501_06121_b300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
 def traffic_from_profiles(kernel_sha):
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
@@ -370,6 +383,7 @@ def main():
     ap.add_argument("--ef", type=int, default=0, help="fix ef instead of sweeping")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-curve", action="store_true")
     ap.add_argument("--serving-seconds", type=float, default=2.0)
     ap.add_argument("--serving-rates", default="5000,20000,50000,100000,200000")
     ap.add_argument("--workload", default="sift1m", choices=["sift1m", "pq768", "sparse100k"])
@@ -494,9 +508,7 @@ def main():
     except Exception:
         pass
     hbm = peaks.get("hbm_gbs", 6400.0)
-    with open(os.path.join(ROOT, "paper_2501_06121_b300", "csrc", "kann_search.cu"), "rb") as f:
-        ksha = hashlib.sha1(f.read()).hexdigest()
-    traffic = traffic_from_profiles(ksha)
+    traffic = traffic_from_profiles(search_kernel_sha())
 
     # ---- end to end through the public API with host buffers
     Qpin = torch.from_numpy(Q).pin_memory()
@@ -529,6 +541,34 @@ def main():
         e2e_ms = float(t.item())
     e2e_qps = world * N_QUERY * args.steps / (e2e_ms / 1e3)
     final_recall = recall_at(ids_buf.cpu().numpy(), gt)
+
+    # recall-QPS curve over the ef sweep (untimed by the step clock; CUDA events
+    # per point), with the achieved fraction of the HBM peak on algorithmic bytes
+    curve = []
+    if rank == 0 and not args.no_curve:
+        for efc in EF_SWEEP:
+            cc = torch.zeros((N_QUERY, 4), dtype=torch.int32, device=dev)
+            K_.kann_search_ex(idx16, Qd, K, efc, rerank=-1, counters=cc, hash_bits=14)
+            torch.cuda.synchronize()
+            m = cc.double().mean(0).cpu().numpy()
+            bq = m[0] * row16 + m[1] * 2 * M * 4 + m[2] * row16 + m[3] * M * 4 + efc * row32 + DIM * 4 + K * 8
+            point = {"ef": efc, "l0_dist_per_query": m[0]}
+            for name, index, rr, rb in (("fp16_rerank", idx16, -1, bq),
+                                        ("fp32", idx32, 0, bq + m[0] * (row32 - row16) + m[2] * (row32 - row16)
+                                         - efc * row32)):
+                for _ in range(2):
+                    K_.kann_search_ex(index, Qd, K, efc, rerank=rr)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+                e0.record()
+                for _ in range(5):
+                    cid_, _ = K_.kann_search_ex(index, Qd, K, efc, rerank=rr)
+                e1.record()
+                torch.cuda.synchronize()
+                msc = e0.elapsed_time(e1) / 5
+                point[name] = {"recall@10": recall_at(cid_.cpu().numpy(), gt), "qps": N_QUERY / (msc / 1e3),
+                               "ms": msc, "roofline_frac": N_QUERY * rb / (msc / 1e3) / 1e9 / hbm}
+            curve.append(point)
 
     serving = None
     if rank == 0 and world == 1 and not args.no_serving:
@@ -565,6 +605,7 @@ def main():
             "clocks": clk,
             "cpu_baseline": cpu_base,
             "serving": serving,
+            "recall_qps_curve": curve,
         }
         print(json.dumps(out))
     if world > 1:

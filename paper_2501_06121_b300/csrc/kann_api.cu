@@ -50,11 +50,6 @@ int lanes_per_row(int nchunks, int chunks_per_lane = 1) {
   return l;
 }
 
-// Chunks per lane used for a storage format by default (measured on the 1M x
-// 128 workload: 64 bytes of an FP32 or E4M3 row per lane, 32 bytes of an FP16
-// or BF16 row).
-int default_chunks_per_lane(int dtype) { return (dtype == KANN_F16 || dtype == KANN_BF16) ? 2 : 4; }
-
 int check_cuda(cudaError_t e) {
   if (e != cudaSuccess) {
     set_cuda_error((int)e);

@@ -60,6 +60,22 @@ struct SparseArgs {
   int vocab;
 };
 
+// Chunks (16 bytes) of a row per lane used for a storage format by default
+// (measured on the 1M x 128 workload: 64 bytes of an FP32 or E4M3 row per
+// lane, 32 bytes of an FP16 or BF16 row).
+constexpr int default_chunks_per_lane(int dtype) { return (dtype == KANN_F16 || dtype == KANN_BF16) ? 2 : 4; }
+
+// A dense/PQ search kernel.
+typedef void (*SearchKernelFn)(const SearchArgs);
+
+// Dense search kernel of one storage format for `cplt` chunks per lane
+// (kann_search_{f32,f16,bf16,e4m3}.cu); lpr_exact > 0 when a row is exactly
+// lpr_exact * cplt chunks.  Null when no kernel exists for the settings.
+SearchKernelFn pick_search_f32(int cplt, bool lean, int metric, int lpr_exact);
+SearchKernelFn pick_search_f16(int cplt, bool lean, int metric, int lpr_exact);
+SearchKernelFn pick_search_bf16(int cplt, bool lean, int metric, int lpr_exact);
+SearchKernelFn pick_search_e4m3(int cplt, bool lean, int metric, int lpr_exact);
+
 // Per-warp shared memory needed by a dense search with these settings.
 int search_warp_smem(int efcap, int hbits);
 int search_warp_smem_pq(int efcap, int hbits, int m);

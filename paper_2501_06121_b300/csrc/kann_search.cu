@@ -1,767 +1,15 @@
-// kann_search.cu -- batched HNSW search kernels for sm_103a.
-//
-// One warp searches one query (HNSW K-NN-SEARCH, Malkov & Yashunin Alg. 5,
-// the index of kANNolo Sec. 2):
-//   1. distance to the entry point;
-//   2. greedy descent through layers max_level..1: move to the (d, id)-best
-//      neighbour while it beats the current node (SEARCH-LAYER with ef = 1);
-//   3. layer-0 beam: W, the ef best (d, id) keys found so far, sorted, each
-//      with an "expanded" bit.  Each step expands the best unexpanded entry:
-//      its adjacency row (M0 ids) is read with one coalesced load per lane,
-//      ids already in the visited table are dropped, the surviving rows are
-//      gathered with 16-byte loads (several rows in flight per warp) and their
-//      distances reduced with shuffles; keys that beat worst(W) are sorted by a
-//      warp bitonic network and merged into W in place (rank by binary search,
-//      move right-to-left).  The search ends when W has no unexpanded entry.
-//      This is the two-heap SEARCH-LAYER (Alg. 2) in its flag-buffer form; both
-//      give the same W under the (d, id) total order;
-//   4. optional exact FP32 re-rank of the best R entries of W;
-//   5. the k best keys are written out (id -1 / +inf padding).
-//
-// The visited table is a per-warp open-addressing hash in shared memory.  It
-// may forget (it is cleared and refilled with W's ids when half full, and an
-// id that finds no slot within the probe window is not stored) but it never
-// reports an unvisited id as visited.  Forgetting is harmless because an id
-// already in W is never inserted twice (equal keys are detected in the merge),
-// and an id that left W or was rejected is worse than worst(W), which only
-// improves once W is full; the search therefore returns the same W as with an
-// exact visited set.  Forgotten ids cost only a repeated distance.
-#include "kann_device.cuh"
-#include "kann_internal.h"
+// kann_search.cu -- launchers of the batched HNSW search kernels, and the PQ
+// and sparse kernels (the dense kernels are compiled per storage format in
+// kann_search_{f32,f16,bf16,e4m3}.cu; all device code is kann_search_impl.cuh).
+#include "kann_search_impl.cuh"
 
 namespace kann {
 namespace {
-
-constexpr u64 FLAG = 0x80000000ull;  // "expanded" bit, kept in the id word
-constexpr uint32_t HEMPTY = 0xffffffffu;
-constexpr int HASH_MAX_PROBE = 32;
-
-__device__ __forceinline__ u64 kmask(u64 k) { return k & ~FLAG; }
-__device__ __forceinline__ uint32_t key_id(u64 k) { return (uint32_t)k & 0x7fffffffu; }
-
-// Visited table.  Returns 0 if id is present, 1 if it was inserted now, 2 if
-// it is absent but the probe window is full (treated as unvisited, not stored).
-__device__ __forceinline__ int visit(uint32_t* H, int hbits, uint32_t id) {
-  const uint32_t mask = (1u << hbits) - 1u;
-  uint32_t h = (id * 2654435761u) >> (32 - hbits);
-  volatile uint32_t* vh = H;
-  for (int p = 0; p < HASH_MAX_PROBE; ++p) {
-    uint32_t v = vh[h];
-    if (v == id) return 0;
-    if (v == HEMPTY) {
-      uint32_t old = atomicCAS(&H[h], HEMPTY, id);
-      if (old == HEMPTY) return 1;
-      if (old == id) return 0;
-    }
-    h = (h + 1u) & mask;
-  }
-  return 2;
-}
-
-__device__ __forceinline__ int lower_bound_w(const u64* W, int len, u64 key) {
-  int lo = 0, hi = len;
-  while (lo < hi) {
-    int mid = (lo + hi) >> 1;
-    if (kmask(W[mid]) < key) lo = mid + 1;
-    else hi = mid;
-  }
-  return lo;
-}
-
-// number of entries of the ascending array A[0..n) that are <= x
-__device__ __forceinline__ int count_le(const int* A, int n, int x) {
-  int lo = 0, hi = n;
-  while (lo < hi) {
-    int mid = (lo + hi) >> 1;
-    if (A[mid] <= x) lo = mid + 1;
-    else hi = mid;
-  }
-  return lo;
-}
-
-// ---------------------------------------------------------------------------
-// Dense back-end: rows of `DT` elements; lanes are split into groups of `lpr`
-// lanes per row, lane `sub` of a group owning 16-byte chunks sub, sub + lpr,
-// ...  (CPL chunks at most).  The query's matching chunks stay in registers.
-// U row-batches are loaded before any is consumed, so U * 32 / lpr rows are
-// in flight per warp.  The summation order of a row's distance depends only
-// on the row, never on its slot in the batch.
-// ---------------------------------------------------------------------------
-template <int DT, int CPL, bool LEAN = false, int MET = KANN_L2>
-struct DenseBackend {
-  static constexpr int EPC = Fmt<DT>::EPC;
-  // row batches in flight: 32 buffer registers per lane, 16 in the lean form
-  static constexpr int U = ((LEAN ? 4 : 8) / CPL) > 0 ? ((LEAN ? 4 : 8) / CPL) : 1;
-  float qr[CPL][EPC];
-
-  __device__ __forceinline__ void init(const SearchArgs& a, int qi, int lane, unsigned char*) {
-    const float* q = a.q + (size_t)qi * a.d;
-    const int sub = lane & (a.lpr - 1);
-#pragma unroll
-    for (int c = 0; c < CPL; ++c) {
-      const int ch = sub + c * a.lpr;
-#pragma unroll
-      for (int e4 = 0; e4 < EPC / 4; ++e4) {
-        float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (ch < a.nchunks) t = __ldg(reinterpret_cast<const float4*>(q + ch * EPC) + e4);
-        qr[c][4 * e4 + 0] = t.x;
-        qr[c][4 * e4 + 1] = t.y;
-        qr[c][4 * e4 + 2] = t.z;
-        qr[c][4 * e4 + 3] = t.w;
-      }
-    }
-  }
-
-  __device__ __forceinline__ void dists(const SearchArgs& a, const int* cid, int cnt, u64* ck, int lane) {
-    const int lpr = a.lpr, rpi = 32 / lpr;
-    const int sub = lane & (lpr - 1), grp = lane / lpr;
-    for (int base = 0; base < cnt; base += rpi * U) {
-      uint4 buf[U][CPL];
-      float sc[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int r = base + u * rpi + grp;
-        const int id = r < cnt ? cid[r] : -1;
-        const unsigned char* row = a.data + (int64_t)(id < 0 ? 0 : id) * a.stride;
-#pragma unroll
-        for (int c = 0; c < CPL; ++c) {
-          const int ch = sub + c * lpr;
-          buf[u][c] = (id >= 0 && ch < a.nchunks) ? ldg_stream16(row + ch * 16) : make_uint4(0u, 0u, 0u, 0u);
-        }
-        sc[u] = 1.f;
-        if (DT == KANN_E4M3) sc[u] = id >= 0 ? __ldg(a.scale + id) : 0.f;
-      }
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int r = base + u * rpi + grp;
-        float acc = 0.f;
-#pragma unroll
-        for (int c = 0; c < CPL; ++c) {
-          float x[EPC];
-          Fmt<DT>::unpack(buf[u][c], x);
-#pragma unroll
-          for (int e = 0; e < EPC; ++e) {
-            const float xv = (DT == KANN_E4M3) ? x[e] * sc[u] : x[e];
-            if (MET == KANN_L2) {
-              const float t = qr[c][e] - xv;
-              acc = fmaf(t, t, acc);
-            } else {
-              acc = fmaf(qr[c][e], xv, acc);
-            }
-          }
-        }
-        for (int o = lpr >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
-        if (sub == 0 && r < cnt) ck[r] = make_key(MET == KANN_L2 ? acc : -acc, (uint32_t)cid[r]);
-      }
-    }
-  }
-};
-
-// ---------------------------------------------------------------------------
-// PQ back-end (asymmetric distance computation, Jegou et al.): the query's
-// table LUT[j][c] = partial distance of query sub-vector j to centroid c of
-// subspace j (L2: ||q_j - C_j[c]||^2, IP: -<q_j, C_j[c]>) is built in FP32
-// in shared memory, then d(q, x) = sum_j LUT[j][code_j(x)].  A row is the m
-// code bytes of an item; lanes own 16-byte chunks of it exactly as in the
-// dense back-end, summing their lookups in byte order.
-// ---------------------------------------------------------------------------
-template <int CPL>
-struct PQBackend {
-  static constexpr int U = (8 / CPL) > 0 ? (8 / CPL) : 1;
-  float* lut;
-
-  __device__ __forceinline__ void init(const SearchArgs& a, int qi, int lane, unsigned char* extra) {
-    lut = reinterpret_cast<float*>(extra);
-    const int m = a.pq_m, dsub = a.pq_dsub;
-    const float* q = a.q + (size_t)qi * m * dsub;
-    for (int e = lane; e < m * 256; e += 32) {
-      const int j = e >> 8;
-      const float* C = a.codebooks + (size_t)e * dsub;
-      const float* qq = q + j * dsub;
-      float s = 0.f;
-      for (int t = 0; t < dsub; ++t) {
-        const float cv = __ldg(C + t), qv = __ldg(qq + t);
-        if (a.metric == KANN_L2) {
-          const float u = qv - cv;
-          s = fmaf(u, u, s);
-        } else {
-          s = fmaf(qv, cv, s);
-        }
-      }
-      lut[e] = a.metric == KANN_L2 ? s : -s;
-    }
-    __syncwarp();
-  }
-
-  __device__ __forceinline__ void dists(const SearchArgs& a, const int* cid, int cnt, u64* ck, int lane) {
-    const int lpr = a.lpr, rpi = 32 / lpr;
-    const int sub = lane & (lpr - 1), grp = lane / lpr;
-    for (int base = 0; base < cnt; base += rpi * U) {
-      uint4 buf[U][CPL];
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int r = base + u * rpi + grp;
-        const int id = r < cnt ? cid[r] : -1;
-        const unsigned char* row = a.codes + (int64_t)(id < 0 ? 0 : id) * a.stride;
-#pragma unroll
-        for (int c = 0; c < CPL; ++c) {
-          const int ch = sub + c * lpr;
-          buf[u][c] = (id >= 0 && ch < a.nchunks) ? ldg_stream16(row + ch * 16) : make_uint4(0u, 0u, 0u, 0u);
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        const int r = base + u * rpi + grp;
-        float acc = 0.f;
-#pragma unroll
-        for (int c = 0; c < CPL; ++c) {
-          const int ch = sub + c * lpr;
-          if (ch < a.nchunks) {
-            const uint32_t w[4] = {buf[u][c].x, buf[u][c].y, buf[u][c].z, buf[u][c].w};
-            const float* L = lut + (size_t)ch * 16 * 256;
-#pragma unroll
-            for (int b = 0; b < 16; ++b) acc += L[b * 256 + ((w[b >> 2] >> (8 * (b & 3))) & 0xffu)];
-          }
-        }
-        for (int o = lpr >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
-        if (sub == 0 && r < cnt) ck[r] = make_key(acc, (uint32_t)cid[r]);
-      }
-    }
-  }
-};
-
-// ---------------------------------------------------------------------------
-// Sparse back-end (inner product over term/weight lists): the query's terms
-// are scattered into a shared-memory hash (term -> weight), then each
-// candidate document's term list is walked by a group of 8 lanes, each lane
-// summing w_q(t) * w_x(t) over its positions in order; distance = -sum.
-// ---------------------------------------------------------------------------
-constexpr int SP_QH = 1024;   // query table slots (queries up to 512 terms)
-constexpr int SP_LPD = 8;     // lanes per document
-
-struct SparseBackend {
-  const SparseArgs* sp;
-  uint32_t* keys;
-  float* vals;
-  uint32_t trunc;
-
-  __device__ __forceinline__ uint32_t slot0(uint32_t t) const { return (t * 2654435761u) >> (32 - 10); }
-
-  __device__ __forceinline__ void init(const SearchArgs& a, int qi, int lane, unsigned char* extra) {
-    keys = reinterpret_cast<uint32_t*>(extra);
-    vals = reinterpret_cast<float*>(keys + SP_QH);
-    trunc = 0;
-    for (int i = lane; i < SP_QH; i += 32) keys[i] = HEMPTY;
-    __syncwarp();
-    const int64_t b = sp->q_indptr[qi], e = sp->q_indptr[qi + 1];
-    for (int64_t t = b + lane; t < e; t += 32) {
-      const uint32_t term = sp->q_terms[t];
-      const float w = sp->q_w[t];
-      uint32_t h = slot0(term);
-      bool done = false;
-      for (int p = 0; p < SP_QH && !done; ++p) {
-        const uint32_t old = atomicCAS(&keys[h], HEMPTY, term);
-        if (old == HEMPTY || old == term) {
-          vals[h] = w;
-          done = true;
-        }
-        h = (h + 1u) & (SP_QH - 1);
-      }
-      if (!done) trunc = 1;
-    }
-    if (e - b > SP_QH / 2) trunc = 1;
-    __syncwarp();
-  }
-
-  __device__ __forceinline__ float weight(uint32_t term) const {
-    uint32_t h = slot0(term);
-    for (int p = 0; p < SP_QH; ++p) {
-      const uint32_t k = keys[h];
-      if (k == term) return vals[h];
-      if (k == HEMPTY) return 0.f;
-      h = (h + 1u) & (SP_QH - 1);
-    }
-    return 0.f;
-  }
-
-  __device__ __forceinline__ void dists(const SearchArgs&, const int* cid, int cnt, u64* ck, int lane) {
-    const int sub = lane & (SP_LPD - 1), grp = lane / SP_LPD;
-    constexpr int DPI = 32 / SP_LPD;  // documents per warp iteration
-    for (int base = 0; base < cnt; base += DPI) {
-      const int r = base + grp;
-      const int id = r < cnt ? cid[r] : -1;
-      float acc = 0.f;
-      if (id >= 0) {
-        const int64_t b = __ldg(sp->indptr + id), e = __ldg(sp->indptr + id + 1);
-        for (int64_t t0 = b + sub; t0 < e; t0 += 4 * SP_LPD) {
-          uint32_t tm[4];
-          float wx[4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int64_t t = t0 + u * SP_LPD;
-            tm[u] = t < e ? (uint32_t)__ldg(sp->terms + t) : HEMPTY;
-            wx[u] = t < e ? __ldg(sp->w + t) : 0.f;
-          }
-#pragma unroll
-          for (int u = 0; u < 4; ++u)
-            if (tm[u] != HEMPTY) acc = fmaf(weight(tm[u]), wx[u], acc);
-        }
-      }
-      for (int o = SP_LPD >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
-      if (sub == 0 && r < cnt) ck[r] = make_key(-acc, (uint32_t)id);
-    }
-  }
-};
-
-// Exact FP32 distances for the re-rank, from the index's FP32 copy.  Same
-// lane/chunk mapping and summation order as the FP32 dense back-end (chunks
-// in order, elements in order, then the butterfly), so a re-ranked distance
-// is bit-identical to the FP32 traversal distance of the same row.
-template <int RDT>
-__device__ __forceinline__ void rerank_dists(const unsigned char* rr, int64_t stride, int nchunks, int lpr, int metric,
-                                             const float* q, const int* cid, int cnt, u64* ck, int lane) {
-  constexpr int U = 4;
-  constexpr int EPC = Fmt<RDT>::EPC;
-  const int rpi = 32 / lpr;
-  const int sub = lane & (lpr - 1), grp = lane / lpr;
-  const int cpl = (nchunks + lpr - 1) / lpr;
-  for (int base = 0; base < cnt; base += rpi * U) {
-    float acc[U];
-    int ids[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int r = base + u * rpi + grp;
-      ids[u] = r < cnt ? cid[r] : -1;
-      acc[u] = 0.f;
-    }
-    for (int c = 0; c < cpl; ++c) {
-      const int ch = sub + c * lpr;
-      float qq[EPC];
-#pragma unroll
-      for (int e4 = 0; e4 < EPC / 4; ++e4) {
-        const float4 qv = ch < nchunks ? __ldg(reinterpret_cast<const float4*>(q + ch * EPC) + e4)
-                                       : make_float4(0.f, 0.f, 0.f, 0.f);
-        qq[4 * e4] = qv.x;
-        qq[4 * e4 + 1] = qv.y;
-        qq[4 * e4 + 2] = qv.z;
-        qq[4 * e4 + 3] = qv.w;
-      }
-      uint4 buf[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u)
-        buf[u] = (ids[u] >= 0 && ch < nchunks) ? ldg_stream16(rr + (int64_t)ids[u] * stride + ch * 16)
-                                               : make_uint4(0u, 0u, 0u, 0u);
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        float x[EPC];
-        Fmt<RDT>::unpack(buf[u], x);
-#pragma unroll
-        for (int e = 0; e < EPC; ++e) {
-          if (metric == KANN_L2) {
-            const float t = qq[e] - x[e];
-            acc[u] = fmaf(t, t, acc[u]);
-          } else {
-            acc[u] = fmaf(qq[e], x[e], acc[u]);
-          }
-        }
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      float v = acc[u];
-      for (int o = lpr >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
-      const int r = base + u * rpi + grp;
-      if (sub == 0 && r < cnt) ck[r] = make_key(metric == KANN_L2 ? v : -v, (uint32_t)ids[u]);
-    }
-  }
-}
-
-// Re-rank the best R entries of W exactly and sort them (cold path, once per
-// query).  Returns the number of re-ranked entries now at the front of W.
-__device__ __noinline__ int rerank_phase(const unsigned char* rr, int rr_dtype, int64_t stride, int nchunks, int lpr,
-                                         int metric, const float* q, int R, u64* W, u64* ck, int* cid, int lane) {
-  for (int b = 0; b < R; b += 64) {
-    const int cb = min(64, R - b);
-    for (int j = lane; j < cb; j += 32) cid[j] = (int)key_id(W[b + j]);
-    __syncwarp();
-    if (rr_dtype == KANN_BF16) rerank_dists<KANN_BF16>(rr, stride, nchunks, lpr, metric, q, cid, cb, ck, lane);
-    else rerank_dists<KANN_F32>(rr, stride, nchunks, lpr, metric, q, cid, cb, ck, lane);
-    __syncwarp();
-    for (int j = lane; j < cb; j += 32) W[b + j] = ck[j];
-    __syncwarp();
-  }
-  int P = 2;
-  while (P < R) P <<= 1;
-  for (int i = R + lane; i < P; i += 32) W[i] = KEY_MAX;
-  __syncwarp();
-  warp_smem_sort(W, P, lane);
-  return R;
-}
-
-// Clear the visited table and put W's ids back (cold path).
-__device__ __noinline__ void reset_visited(uint32_t* H, int hbits, const u64* W, int len, int lane) {
-  for (int i = lane; i < (1 << hbits); i += 32) H[i] = HEMPTY;
-  __syncwarp();
-  for (int i = lane; i < len; i += 32) visit(H, hbits, key_id(W[i]));
-  __syncwarp();
-}
-
-// Survivors of a step (keys that beat worst(W) and are not in W) ordered by a
-// bitonic network, repeats inside the batch dropped; writes the ordered keys
-// and their W-ranks to ck/clb and returns their number.  Used when a step has
-// many survivors or repeated keys (cold path).
-__device__ __noinline__ int order_by_sort(u64 e0, u64 e1, bool k0, bool k1, const u64* W, int len, u64* ck, int* clb,
-                                          int lane) {
-  const unsigned lt = (1u << lane) - 1u;
-  if (!k0) e0 = KEY_MAX;
-  if (!k1) e1 = KEY_MAX;
-  if (__ballot_sync(FULL, k1)) warp_sort64(e0, e1, lane);
-  else e0 = warp_sort32(e0, lane);
-  const u64 last0 = __shfl_sync(FULL, e0, 31);
-  const u64 up0 = __shfl_up_sync(FULL, e0, 1);
-  const u64 up1 = __shfl_up_sync(FULL, e1, 1);
-  const bool ok0 = e0 != KEY_MAX && !(lane > 0 && e0 == up0);
-  const bool ok1 = e1 != KEY_MAX && !(lane > 0 ? e1 == up1 : e1 == last0);
-  const int lb0 = ok0 ? lower_bound_w(W, len, e0) : 0;
-  const int lb1 = ok1 ? lower_bound_w(W, len, e1) : 0;
-  const unsigned s0 = __ballot_sync(FULL, ok0), s1 = __ballot_sync(FULL, ok1);
-  const int cs0 = __popc(s0);
-  __syncwarp();
-  if (ok0) {
-    ck[__popc(s0 & lt)] = e0;
-    clb[__popc(s0 & lt)] = lb0;
-  }
-  if (ok1) {
-    ck[cs0 + __popc(s1 & lt)] = e1;
-    clb[cs0 + __popc(s1 & lt)] = lb1;
-  }
-  return cs0 + __popc(s1);
-}
-
-// Shared memory of one warp: W[efcap] keys, candidate keys[64], candidate
-// ids[64], candidate W-ranks[64], then the visited table (1 << hbits words),
-// then back-end scratch.
-struct WarpSmem {
-  u64* W;
-  u64* ck;
-  int* cid;
-  int* clb;
-  uint32_t* H;
-  unsigned char* extra;
-  __device__ __forceinline__ WarpSmem(unsigned char* ws, int efcap, int hbits) {
-    W = reinterpret_cast<u64*>(ws);
-    ck = W + efcap;
-    cid = reinterpret_cast<int*>(ck + 64);
-    clb = cid + 64;
-    H = reinterpret_cast<uint32_t*>(clb + 64);
-    extra = reinterpret_cast<unsigned char*>(H + (1 << hbits));
-  }
-};
-
-template <class B>
-__device__ __forceinline__ uint32_t backend_status(const B&) { return 0u; }
-__device__ __forceinline__ uint32_t backend_status(const SparseBackend& b) {
-  return b.trunc ? KANN_QSTAT_QUERY_TRUNCATED : 0u;
-}
-
-template <class B>
-__device__ __forceinline__ void search_one(const SearchArgs& a, B& be, int qi, int lane, unsigned char* ws) {
-  WarpSmem s(ws, a.efcap, a.hbits);
-  u64* W = s.W;
-  u64* ck = s.ck;
-  int* cid = s.cid;
-  int* clb = s.clb;
-  uint32_t* H = s.H;
-  const int Hn = 1 << a.hbits;
-  const unsigned lt = (1u << lane) - 1u;
-
-  int k = a.k, ef = a.ef;
-  if (a.k_arr) {
-    k = min(max(a.k_arr[qi], 1), a.kmax);
-    ef = a.ef_arr[qi];
-  }
-  ef = min(max(ef, k), a.efmax);
-  uint32_t st = 0;
-  int c_l0d = 0, c_l0e = 0, c_upd = 0, c_uph = 0;
-
-  be.init(a, qi, lane, s.extra);
-  st |= backend_status(be);
-
-  // 1. entry point
-  if (lane == 0) cid[0] = a.entry;
-  __syncwarp();
-  be.dists(a, cid, 1, ck, lane);
-  __syncwarp();
-  u64 cur = ck[0];
-  c_upd = 1;
-  __syncwarp();
-
-  // 2. greedy descent through the upper layers
-  for (int l = a.max_level; l >= 1; --l) {
-    for (;;) {
-      const int cur_id = (int)key_id(cur);
-      const int slot = __ldg(a.upper_slot + cur_id);
-      int v = -1;
-      if (slot >= 0 && lane < a.M) v = __ldg(a.upper + ((int64_t)slot * a.max_level + (l - 1)) * a.M + lane);
-      if (slot < 0 || v >= a.n) st |= KANN_QSTAT_BAD_ID;
-      if (v >= a.n) v = -1;
-      const bool ok = v >= 0;
-      const unsigned bal = __ballot_sync(FULL, ok);
-      const int cnt = __popc(bal);
-      if (ok) cid[__popc(bal & lt)] = v;
-      __syncwarp();
-      be.dists(a, cid, cnt, ck, lane);
-      __syncwarp();
-      c_upd += cnt;
-      ++c_uph;
-      const u64 best = warp_min64(lane < cnt ? ck[lane] : KEY_MAX);
-      __syncwarp();
-      if (best < cur) cur = best;
-      else break;
-    }
-  }
-
-  // 3. layer-0 beam
-  for (int i = lane; i < Hn; i += 32) H[i] = HEMPTY;
-  __syncwarp();
-  if (lane == 0) {
-    visit(H, a.hbits, key_id(cur));
-    W[0] = cur;
-  }
-  __syncwarp();
-  int len = 1, cursor = 0, hops = 0, stored = 1;
-  for (;;) {
-    int p = -1;
-    for (int b = cursor; b < len; b += 32) {
-      const int i = b + lane;
-      const bool un = i < len && !(W[i] & FLAG);
-      const unsigned m = __ballot_sync(FULL, un);
-      if (m) {
-        p = b + __ffs(m) - 1;
-        break;
-      }
-    }
-    if (p < 0) break;
-    if (hops >= a.max_hops) {
-      st |= KANN_QSTAT_HOPCAP;
-      break;
-    }
-    ++hops;
-    const u64 ce = W[p];
-    __syncwarp();
-    if (lane == 0) W[p] = ce | FLAG;
-    cursor = p + 1;
-    const int c_id = (int)key_id(ce);
-    const int32_t* nb = a.l0 + (int64_t)c_id * a.M0;
-    int v0 = lane < a.M0 ? __ldg(nb + lane) : -1;
-    int v1 = lane + 32 < a.M0 ? __ldg(nb + 32 + lane) : -1;
-    if (v0 >= a.n || v1 >= a.n) st |= KANN_QSTAT_BAD_ID;
-    if (v0 >= a.n) v0 = -1;
-    if (v1 >= a.n) v1 = -1;
-    const int r0 = v0 >= 0 ? visit(H, a.hbits, (uint32_t)v0) : 0;
-    const int r1 = v1 >= 0 ? visit(H, a.hbits, (uint32_t)v1) : 0;
-    stored += __popc(__ballot_sync(FULL, r0 == 1)) + __popc(__ballot_sync(FULL, r1 == 1));
-    const unsigned b0 = __ballot_sync(FULL, r0 != 0), b1 = __ballot_sync(FULL, r1 != 0);
-    const int c0 = __popc(b0), cnt = c0 + __popc(b1);
-    if (r0) cid[__popc(b0 & lt)] = v0;
-    if (r1) cid[c0 + __popc(b1 & lt)] = v1;
-    __syncwarp();
-    ++c_l0e;
-    if (cnt > 0) {
-      be.dists(a, cid, cnt, ck, lane);
-      __syncwarp();
-      c_l0d += cnt;
-      // survivors: keys that beat worst(W) and are not in W already
-      const u64 worst = len >= ef ? kmask(W[len - 1]) : KEY_MAX;
-      const u64 e0 = lane < cnt ? ck[lane] : KEY_MAX;
-      const u64 e1 = lane + 32 < cnt ? ck[lane + 32] : KEY_MAX;
-      bool k0 = e0 < worst, k1 = e1 < worst;
-      int lb0 = 0, lb1 = 0;
-      if (k0) {
-        lb0 = lower_bound_w(W, len, e0);
-        k0 = !(lb0 < len && kmask(W[lb0]) == e0);
-      }
-      if (k1) {
-        lb1 = lower_bound_w(W, len, e1);
-        k1 = !(lb1 < len && kmask(W[lb1]) == e1);
-      }
-      const unsigned s0 = __ballot_sync(FULL, k0), s1 = __ballot_sync(FULL, k1);
-      const int c = __popc(s0) + __popc(s1);
-      int cnew = 0;
-      if (c > 0) {
-        bool sorted = false;
-        if (c <= 16) {
-          // rank of a survivor = number of survivors with a smaller key
-          int r0 = 0, r1 = 0;
-          bool d0 = false, d1 = false;
-          for (unsigned m = s0; m; m &= m - 1) {
-            const int src = __ffs(m) - 1;
-            const u64 x = __shfl_sync(FULL, e0, src);
-            r0 += x < e0;
-            r1 += x < e1;
-            d0 |= (x == e0) && (src < lane);
-            d1 |= x == e1;
-          }
-          for (unsigned m = s1; m; m &= m - 1) {
-            const int src = __ffs(m) - 1;
-            const u64 x = __shfl_sync(FULL, e1, src);
-            r0 += x < e0;
-            r1 += x < e1;
-            d1 |= (x == e1) && (src < lane);
-          }
-          // a key repeated inside the batch (possible only after the visited
-          // table forgot, with a repeated edge) takes the sorting path
-          if (__ballot_sync(FULL, (k0 && d0) || (k1 && d1)) == 0) {
-            __syncwarp();
-            if (k0) {
-              ck[r0] = e0;
-              clb[r0] = lb0;
-            }
-            if (k1) {
-              ck[r1] = e1;
-              clb[r1] = lb1;
-            }
-            cnew = c;
-            sorted = true;
-          }
-        }
-        if (!sorted) cnew = order_by_sort(e0, e1, k0, k1, W, len, ck, clb, lane);
-        __syncwarp();
-        // merge: move W[lo..len) right by the number of survivors ranked before
-        // each entry, last chunk first, then drop the survivors in place
-        const int lo = clb[0];
-        for (int top = len; top > lo; top -= 32) {
-          const int i = top - 32 + lane;
-          const bool act = i >= lo;
-          u64 val = 0;
-          int dest = 0;
-          if (act) {
-            val = W[i];
-            dest = i + count_le(clb, cnew, i);
-          }
-          __syncwarp();
-          if (act && dest < ef) W[dest] = val;
-          __syncwarp();
-        }
-        for (int j = lane; j < cnew; j += 32) {
-          const int pos = j + clb[j];
-          if (pos < ef) W[pos] = ck[j];
-        }
-        __syncwarp();
-        len = min(len + cnew, ef);
-        if (lo < cursor) cursor = lo;
-      }
-    }
-    // visited-table upkeep: keep the load factor at or below one half
-    if (stored > (Hn >> 1)) {
-      st |= KANN_QSTAT_FORGOT;
-      reset_visited(H, a.hbits, W, len, lane);
-      stored = len;
-    }
-  }
-
-  // 4. exact re-rank of the best R entries
-  int nout = len;
-  if (a.R != 0 && a.rr_data != nullptr) {
-    const int R = min(a.R < 0 ? ef : a.R, len);
-    nout = rerank_phase(a.rr_data, a.rr_dtype, a.rr_stride, a.rr_nchunks, a.rr_lpr, a.metric, a.q + (size_t)qi * a.d, R, W, ck,
-                        cid, lane);
-  }
-
-  // 5. output
-  const int ld = a.k_arr ? a.kmax : a.k;
-  for (int j = lane; j < ld; j += 32) {
-    int32_t id = -1;
-    float dd = __int_as_float(0x7f800000);
-    if (j < k && j < nout) {
-      const u64 key = kmask(W[j]);
-      id = (int32_t)key_id(key);
-      dd = key_dist(key);
-    }
-    a.out_ids[(size_t)qi * ld + j] = id;
-    a.out_d[(size_t)qi * ld + j] = dd;
-  }
-  st = __reduce_or_sync(FULL, st);
-  if (lane == 0) {
-    if (a.status) a.status[qi] = st;
-    if (a.counters) {
-      a.counters[(size_t)qi * 4 + 0] = c_l0d;
-      a.counters[(size_t)qi * 4 + 1] = c_l0e;
-      a.counters[(size_t)qi * 4 + 2] = c_upd;
-      a.counters[(size_t)qi * 4 + 3] = c_uph;
-    }
-  }
-}
-
-// Register budget from the query registers a lane holds: <= 8 -> 64
-// registers (32 warps per SM), <= 16 -> 80 (24 warps), wider -> 128.  The
-// lean form (half the rows in flight) always asks for 64 when q <= 16.
-template <int DT, int CPLT, bool LEAN>
-struct MinBlocks {
-  static constexpr int q = CPLT * Fmt<DT>::EPC;
-  static constexpr int value = q <= 8 ? 8 : (q <= 16 ? (LEAN ? 8 : 6) : 4);
-};
-
-// Queries of one launch: a plain grid gives warp w of CTA b query
-// b * warps + w; the persistent form has every warp take the next query index
-// from a device counter until the batch is exhausted (work stealing: a warp
-// that finishes a cheap query starts the next one at once).
-template <class B>
-__device__ __forceinline__ void run_queries(const SearchArgs& a, B& be) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  unsigned char* ws = smem + (size_t)warp * a.warp_smem;
-  if (a.work_counter == nullptr) {
-    const int qi = blockIdx.x * (blockDim.x >> 5) + warp;
-    if (qi < a.nq) search_one<B>(a, be, qi, lane, ws);
-    return;
-  }
-  int nq = a.nq;
-  if (a.d_n) nq = min(nq, max(0, *a.d_n));
-  for (;;) {
-    int qi = 0;
-    if (lane == 0) qi = atomicAdd(a.work_counter, 1);
-    qi = __shfl_sync(FULL, qi, 0);
-    if (qi >= nq) break;
-    search_one<B>(a, be, qi, lane, ws);
-  }
-}
-
-template <int DT, int CPLT, bool LEAN, int MET>
-__global__ void __launch_bounds__(128, MinBlocks<DT, CPLT, LEAN>::value) search_dense_kernel(const SearchArgs a) {
-  DenseBackend<DT, CPLT, LEAN, MET> be;
-  run_queries(a, be);
-}
-
-template <int CPLT>
-__global__ void __launch_bounds__(128, 1) search_pq_kernel(const SearchArgs a) {
-  PQBackend<CPLT> be;
-  run_queries(a, be);
-}
 
 __global__ void __launch_bounds__(128, 4) search_sparse_kernel(const SearchArgs a, const __grid_constant__ SparseArgs sp) {
   SparseBackend be;
   be.sp = &sp;
   run_queries(a, be);
-}
-
-typedef void (*KernelFn)(const SearchArgs);
-
-template <int DT, int MET>
-KernelFn pick_dense_m(int cplt, bool lean) {
-  switch (cplt * 2 + (lean ? 1 : 0)) {
-    case 2: return search_dense_kernel<DT, 1, false, MET>;
-    case 4: return search_dense_kernel<DT, 2, false, MET>;
-    case 5: return search_dense_kernel<DT, 2, true, MET>;
-    case 8: return search_dense_kernel<DT, 4, false, MET>;
-    case 16: return search_dense_kernel<DT, 8, false, MET>;
-    default: return nullptr;
-  }
-}
-
-template <int DT>
-KernelFn pick_dense(int cplt, bool lean, int metric) {
-  return metric == KANN_L2 ? pick_dense_m<DT, KANN_L2>(cplt, lean) : pick_dense_m<DT, KANN_IP>(cplt, lean);
 }
 
 // Grid of a launch: one warp per query, or (persistent) as many CTAs as fit
@@ -799,12 +47,13 @@ int search_warp_smem(int efcap, int hbits) {
 int launch_search_dense(const SearchArgs& a, int dtype, int wpb, void* stream) {
   if (a.nq == 0) return 0;
   const int cplt = pow2_at_least((a.nchunks + a.lpr - 1) / a.lpr);
-  KernelFn fn = nullptr;
+  const int lpr_exact = a.nchunks == a.lpr * cplt ? a.lpr : 0;
+  SearchKernelFn fn = nullptr;
   switch (dtype) {
-    case KANN_F32: fn = pick_dense<KANN_F32>(cplt, a.lean, a.metric); break;
-    case KANN_F16: fn = pick_dense<KANN_F16>(cplt, a.lean, a.metric); break;
-    case KANN_BF16: fn = pick_dense<KANN_BF16>(cplt, a.lean, a.metric); break;
-    case KANN_E4M3: fn = pick_dense<KANN_E4M3>(cplt, a.lean, a.metric); break;
+    case KANN_F32: fn = pick_search_f32(cplt, a.lean, a.metric, lpr_exact); break;
+    case KANN_F16: fn = pick_search_f16(cplt, a.lean, a.metric, lpr_exact); break;
+    case KANN_BF16: fn = pick_search_bf16(cplt, a.lean, a.metric, lpr_exact); break;
+    case KANN_E4M3: fn = pick_search_e4m3(cplt, a.lean, a.metric, lpr_exact); break;
     default: break;
   }
   if (!fn) return (int)cudaErrorInvalidValue;
@@ -825,7 +74,7 @@ int search_warp_smem_sparse(int efcap, int hbits) { return search_warp_smem(efca
 int launch_search_pq(const SearchArgs& a, int wpb, void* stream) {
   if (a.nq == 0) return 0;
   const int cplt = pow2_at_least((a.nchunks + a.lpr - 1) / a.lpr);
-  KernelFn fn = nullptr;
+  SearchKernelFn fn = nullptr;
   if (cplt == 1) fn = search_pq_kernel<1>;
   if (cplt == 2) fn = search_pq_kernel<2>;
   if (cplt == 4) fn = search_pq_kernel<4>;

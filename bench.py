@@ -362,13 +362,16 @@ def search_kernel_sha():
     return h.hexdigest()
 
 
-def traffic_from_profiles(kernel_sha):
+def traffic_from_profiles(kernel_sha, ef):
+    """DRAM bytes (read + write) of one search launch at this ef, from the
+    ncu counters stored in profiles/traffic.json, or None when none were taken
+    for this kernel source and ef."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             t = json.load(f)
         if t.get("kernel_source_sha1") == kernel_sha:
-            return t.get("dram_bytes_per_launch")
+            return t.get("dram_bytes_per_launch_by_ef", {}).get(str(ef))
     except Exception:
         pass
     return None
@@ -454,6 +457,20 @@ def main():
             break
     if ef_sel is None:
         ef_sel = EF_SWEEP[-1]
+    elif not args.ef and ef_sel != EF_SWEEP[0]:
+        # refine between the last sweep value below the target and ef_sel
+        lo = EF_SWEEP[EF_SWEEP.index(ef_sel) - 1]
+        step = max(1, (ef_sel - lo) // 4)
+        for efr in range(lo + step, ef_sel, step):
+            ids, _ = K_.kann_search_ex(idx16, Qd, K, efr, rerank=-1)
+            torch.cuda.synchronize()
+            rec = recall_at(ids.cpu().numpy(), gt)
+            i32, _ = K_.kann_search_ex(idx32, Qd, K, efr)
+            torch.cuda.synchronize()
+            sweep[efr] = {"recall_fp16_rerank": rec, "recall_fp32": recall_at(i32.cpu().numpy(), gt)}
+            if rec >= 0.95:
+                ef_sel = efr
+                break
     ef = ef_sel
 
     # algorithmic work per query (large visited table: no repeated distances)
@@ -508,7 +525,7 @@ def main():
     except Exception:
         pass
     hbm = peaks.get("hbm_gbs", 6400.0)
-    traffic = traffic_from_profiles(search_kernel_sha())
+    traffic = traffic_from_profiles(search_kernel_sha(), ef)
 
     # ---- end to end through the public API with host buffers
     Qpin = torch.from_numpy(Q).pin_memory()
@@ -588,7 +605,8 @@ def main():
                        "storage": "f16 traversal + f32 re-rank (R = ef)", "parallelism": "replicas%d" % world,
                        "l2": "inputs larger than L2 (f16 base 256 MB + f32 base 512 MB + graph 256 MB)",
                        "fp32_plain_qps": N_QUERY * world / (fp32_ms / 1e3), "fp32_plain_ms_per_step": fp32_ms,
-                       "ef_sweep": sweep, "graph_build_s": build_s, "graph_cached": cached,
+                       "ef_sweep": {str(e): sweep[e] for e in sorted(sweep)}, "graph_build_s": build_s,
+                       "graph_cached": cached,
                        "ground_truth_s": gt_s,
                        "batch_latency_ms": {"p50": per_sorted[len(per) // 2],
                                             "p99": per_sorted[min(len(per) - 1, int(0.99 * len(per)))]},

@@ -20,6 +20,13 @@
 //               reads its scores with tcgen05.ld into registers, filters them
 //               against its current k-th distance and inserts the survivors
 //               into its own top-k list in shared memory.
+// The scans of one query (its 2 S column-half x split lists, on different
+// CTAs) share an upper bound on its k-th score in global memory: it starts
+// from tc_threshold_kernel's bound (a strided sample of the base scored on the
+// CUDA cores), every list that is full lowers it (atomicMin) to just above its
+// own k-th score, and each scan filters against the smaller of that bound and
+// its own k-th.  Any list's k-th bounds the union's from above, so nothing
+// that belongs in the top k is dropped, and the insert path stays rare.
 // Accumulators are double-buffered so the epilogue of tile t overlaps the
 // MMAs of tile t+1.  Every mbarrier wait is bounded by a %globaltimer
 // deadline; on expiry the CTA raises an error flag and all roles wind down,
@@ -58,6 +65,7 @@ struct TcArgs {
   uint32_t idesc;
   const float* xnorm;   // [nb]
   const float* qnorm;   // [nq]
+  unsigned* thr;        // [nq] shared upper bound on each query's k-th score (ordered_bits code)
   u64* out;             // [nq][S][k] partial lists
   int* err;
 };
@@ -193,17 +201,27 @@ __device__ __forceinline__ void tc_ld64(uint32_t taddr, float* v) {
   for (int i = 0; i < 64; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Inverse of ordered_bits.
+__device__ __forceinline__ float from_ordered(unsigned b) {
+  return __uint_as_float((b & 0x80000000u) ? (b & 0x7fffffffu) : ~b);
+}
+
 // A thread's top-k list lives in shared memory (its own k slots); the
 // registers hold the current worst entry's distance and slot.
-struct TopkWorst {
-  float thr;
-  int slot;
+// Scan state of one thread: its own list's k-th score and slot, and the
+// query's shared bound as last seen.
+struct ScanState {
+  float thr;    // own list's k-th score (+inf until the list is full)
+  int slot;     // slot holding it
+  float thr_g;  // shared bound on the query's k-th score
 };
 
-// Put (dist, col) in the worst slot and find the new worst by (d, id).
-__device__ __noinline__ TopkWorst topk_insert(float* ld, int* li, int k, int slot, float dist, int col) {
-  ld[slot] = dist;
-  li[slot] = col;
+// Put (dist, col) in the worst slot, find the new worst by (d, id), and when
+// the list is full publish just above its k-th score as the query's bound.
+__device__ __noinline__ ScanState topk_insert(float* ld, int* li, int k, ScanState w, float dist, int col,
+                                              unsigned* thr_q) {
+  ld[w.slot] = dist;
+  li[w.slot] = col;
   float wd = -__int_as_float(0x7f800000);
   int wid = -2, wi = 0;
   for (int m = 0; m < k; ++m) {
@@ -215,7 +233,16 @@ __device__ __noinline__ TopkWorst topk_insert(float* ld, int* li, int k, int slo
       wi = m;
     }
   }
-  return TopkWorst{wd, wi};
+  w.thr = wd;
+  w.slot = wi;
+  if (wd != __int_as_float(0x7f800000)) {
+    const float up = nextafterf(wd, __int_as_float(0x7f800000));
+    if (up < w.thr_g) {
+      w.thr_g = up;
+      atomicMin(thr_q, ordered_bits(up));
+    }
+  }
+  return w;
 }
 
 // ---- the kernel ------------------------------------------------------------
@@ -330,10 +357,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         ld[j] = __int_as_float(0x7f800000);
         li[j] = -1;
       }
-      TopkWorst w{__int_as_float(0x7f800000), 0};
+      // rows past nq (the zero-filled tail of the last query tile) never
+      // insert, so they never publish a bound
+      ScanState w{q < a.nq ? __int_as_float(0x7f800000) : -__int_as_float(0x7f800000), 0,
+                  q < a.nq ? from_ordered(__ldcg(a.thr + q)) : __int_as_float(0x7f800000)};
+      unsigned* thr_q = a.thr + (q < a.nq ? q : 0);
       for (int64_t b0 = b_begin; b0 < b_end; b0 += TC_N, ++t) {
         const uint32_t buf = t & 1u, use = t >> 1;
         const int64_t c_base = b0 + grp * 128;
+        const unsigned thr_code = q < a.nq ? __ldcg(a.thr + q) : 0xff800000u;  // other lists' progress (+inf)
         if (a.metric == KANN_L2)
           for (int j = lane; j < 128; j += 32) xw[j] = (c_base + j < b_end) ? __ldg(a.xnorm + c_base + j) : 0.f;
         __syncwarp();
@@ -345,30 +377,44 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           float v[64];
           tc_ld64(tmem + ((uint32_t)(quarter * 32) << 16) + buf * TC_N + grp * 128 + c0, v);
           const int64_t cb = c_base + c0;
-          // pass 1: distances and a mask of those that beat the current k-th
-          uint32_t m0 = 0u, m1 = 0u;
+          // pass 1: scores and the minimum of each group of 16 columns
+          float mn[4];
 #pragma unroll
-          for (int j = 0; j < 64; j += 4) {
-            float4 n4 = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (a.metric == KANN_L2) n4 = *reinterpret_cast<const float4*>(xw + c0 + j);
-            const float nn[4] = {n4.x, n4.y, n4.z, n4.w};
+          for (int g = 0; g < 4; ++g) {
+            mn[g] = __int_as_float(0x7f800000);
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-              v[j + u] = a.metric == KANN_L2 ? fmaf(-2.f, v[j + u], nn[u]) : -v[j + u];
-              const uint32_t bit = v[j + u] < w.thr ? 1u : 0u;
-              if (j + u < 32) m0 |= bit << (j + u);
-              else m1 |= bit << (j + u - 32);
+            for (int j = 16 * g; j < 16 * g + 16; j += 4) {
+              if (a.metric == KANN_L2) {
+                const float4 n4 = *reinterpret_cast<const float4*>(xw + c0 + j);
+                v[j] = fmaf(-2.f, v[j], n4.x);
+                v[j + 1] = fmaf(-2.f, v[j + 1], n4.y);
+                v[j + 2] = fmaf(-2.f, v[j + 2], n4.z);
+                v[j + 3] = fmaf(-2.f, v[j + 3], n4.w);
+              } else {
+                v[j] = -v[j];
+                v[j + 1] = -v[j + 1];
+                v[j + 2] = -v[j + 2];
+                v[j + 3] = -v[j + 3];
+              }
+              mn[g] = fminf(mn[g], fminf(fminf(v[j], v[j + 1]), fminf(v[j + 2], v[j + 3])));
             }
           }
-          // pass 2 (rare once the list is full): insert in column order;
-          // columns arrive in increasing id order, so a tie never enters
-          if (m0 | m1) {
-            const bool tail = cb + 64 > b_end;
+          // pass 2 (rare: a score beats the current bound), per group of 16
+          // columns: insert in column order; columns arrive in increasing id
+          // order, so a tie with this list's own k-th never enters
+          w.thr_g = fminf(w.thr_g, from_ordered(thr_code));
+          float eff = fminf(w.thr, w.thr_g);
+          const bool tail = cb + 64 > b_end;
 #pragma unroll
-            for (int j = 0; j < 64; ++j) {
-              const bool bit = ((j < 32 ? m0 >> j : m1 >> (j - 32)) & 1u) != 0u;
-              if (bit && v[j] < w.thr && (!tail || cb + j < b_end))
-                w = topk_insert(ld, li, a.k, w.slot, v[j], (int)(cb + j));
+          for (int g = 0; g < 4; ++g) {
+            if (mn[g] < eff) {
+#pragma unroll
+              for (int j = 16 * g; j < 16 * g + 16; ++j) {
+                if (v[j] < eff && (!tail || cb + j < b_end)) {
+                  w = topk_insert(ld, li, a.k, w, v[j], (int)(cb + j), thr_q);
+                  eff = fminf(w.thr, w.thr_g);
+                }
+              }
             }
           }
         }
@@ -411,6 +457,69 @@ __global__ void row_norms_kernel(const uint16_t* __restrict__ x, int64_t n, int 
   }
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL, s, o);
   if (lane == 0) out[row] = s;
+}
+
+constexpr int TH_SAMPLE = 1024;  // base rows scored per query for the starting threshold
+
+// Starting threshold of each query's scan (one warp per query).  Every lane
+// scores a strided sample of base rows exactly as the epilogue does (L2:
+// ||x||^2 - 2 q.x, IP: -q.x; the query's own constant left out) but in FP32
+// on the CUDA cores, raises each score by a bound on the difference between
+// two FP32 evaluations of the same dot product in any summation order (the
+// products of 16-bit inputs are exact; with unit roundoff taken as 2^-23,
+// d terms, S = sum |q_i x_i|: 2 * d * 2^-23 * S per evaluation, doubled for
+// L2's factor 2, plus the final roundings), and keeps its minimum.  The k-th
+// smallest lane minimum comes from k distinct rows, so it is at least the
+// k-th smallest tensor-core score of the whole base: no neighbour that
+// belongs in the top k is pruned.  thr (an ordered_bits code) is stored just
+// above it because the scan keeps scores strictly below the threshold.
+template <int DT>
+__global__ void tc_threshold_kernel(const uint16_t* __restrict__ Q, const uint16_t* __restrict__ X, int nq,
+                                    int64_t nb, int d, int metric, int k, const float* __restrict__ xnorm,
+                                    unsigned* __restrict__ thr) {
+  const int lane = threadIdx.x & 31;
+  const int64_t q = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (q >= nq) return;
+  const float inf = __int_as_float(0x7f800000);
+  const float u = 1.0f / 8388608.0f;  // 2^-23
+  const int64_t T = nb < TH_SAMPLE ? nb : TH_SAMPLE;
+  const uint16_t* qp = Q + q * d;
+  float mn = inf;
+  for (int64_t j = lane; j < T; j += 32) {
+    const int64_t r = j * nb / T;  // distinct rows, since T <= nb
+    const uint16_t* xp = X + r * d;
+    float dot = 0.f, sab = 0.f;
+    for (int c = 0; c < d; c += 8) {
+      float xv[8], qv[8];
+      Fmt<DT>::unpack(*reinterpret_cast<const uint4*>(xp + c), xv);
+      Fmt<DT>::unpack(*reinterpret_cast<const uint4*>(qp + c), qv);
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        dot = fmaf(xv[e], qv[e], dot);
+        sab += fabsf(xv[e] * qv[e]);
+      }
+    }
+    float v, margin;
+    if (metric == KANN_L2) {
+      const float xn = xnorm[r];
+      v = fmaf(-2.f, dot, xn);
+      margin = 8.f * (float)d * u * sab + 4.f * u * (fabsf(v) + xn + 2.f * sab);
+    } else {
+      v = -dot;
+      margin = 4.f * (float)d * u * sab + 4.f * u * sab;
+    }
+    float vu = v + margin;
+    vu = vu + 4.f * u * fabsf(vu) + 1e-30f;
+    if (!(vu == vu)) vu = inf;  // NaN input: no pruning
+    mn = fminf(mn, vu);
+  }
+  // k-th smallest of the 32 lane minima
+  const u64 key = warp_sort32(((u64)ordered_bits(mn) << 32) | (uint32_t)lane, lane);
+  const u64 kth = __shfl_sync(FULL, key, k - 1);
+  if (lane == 0) {
+    const float t = key_dist(kth);
+    thr[q] = ordered_bits(t == inf ? inf : nextafterf(t, inf));
+  }
 }
 
 // Final merge: sort each query's S*k partial keys, keep k (an error flag
@@ -497,7 +606,7 @@ size_t exact_tc_workspace_bytes(int nq, int64_t nb, int k) {
   int S;
   int64_t per;
   exact_tc_plan(nq, nb, &S, &per);
-  return (size_t)nq * S * 2 * k * 8 + (size_t)nb * 4 + (size_t)nq * 4 + 256;
+  return (size_t)nq * S * 2 * k * 8 + (size_t)nb * 4 + (size_t)nq * 8 + 256;
 }
 
 bool exact_tc_supported(int dtype, int d, int k) {
@@ -513,7 +622,8 @@ int exact_tc_run(const void* Q, const void* X, int nq, int64_t nb, int d, int me
   u64* part = reinterpret_cast<u64*>(w);
   float* xn = reinterpret_cast<float*>(w + (size_t)nq * S * 2 * k * 8);
   float* qn = xn + nb;
-  int* err = reinterpret_cast<int*>(((uintptr_t)(qn + nq) + 15) & ~(uintptr_t)15);
+  unsigned* th = reinterpret_cast<unsigned*>(qn + nq);
+  int* err = reinterpret_cast<int*>(((uintptr_t)(th + nq) + 15) & ~(uintptr_t)15);
   CUtensorMap mq, mx;
   if (!make_map(&mq, Q, dtype, d, nq, TC_M) || !make_map(&mx, X, dtype, d, nb, TC_N)) return (int)cudaErrorInvalidValue;
   cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), s);
@@ -522,6 +632,10 @@ int exact_tc_run(const void* Q, const void* X, int nq, int64_t nb, int d, int me
       dtype == KANN_BF16 ? row_norms_kernel<KANN_BF16> : row_norms_kernel<KANN_F16>;
   nfn<<<(unsigned)((nb * 32 + 255) / 256), 256, 0, s>>>((const uint16_t*)X, nb, d, xn);
   nfn<<<(unsigned)(((int64_t)nq * 32 + 255) / 256), 256, 0, s>>>((const uint16_t*)Q, nq, d, qn);
+  void (*tfn)(const uint16_t*, const uint16_t*, int, int64_t, int, int, int, const float*, unsigned*) =
+      dtype == KANN_BF16 ? tc_threshold_kernel<KANN_BF16> : tc_threshold_kernel<KANN_F16>;
+  tfn<<<(unsigned)(((int64_t)nq * 32 + 255) / 256), 256, 0, s>>>((const uint16_t*)Q, (const uint16_t*)X, nq, nb, d,
+                                                                  metric, k, xn, th);
   TcArgs a;
   a.nq = nq;
   a.nb = nb;
@@ -535,6 +649,7 @@ int exact_tc_run(const void* Q, const void* X, int nq, int64_t nb, int d, int me
   a.idesc = make_idesc(dtype);
   a.xnorm = xn;
   a.qnorm = qn;
+  a.thr = th;
   a.out = part;
   a.err = err;
   // shared memory: alignment pad, stage ring, barriers, norms, top-k lists

@@ -23,7 +23,8 @@ def to16(a, dtype):
 
 
 @pytest.mark.parametrize("nq,nb,d,hi", [(300, 5000, 128, 256), (1, 1000, 64, 256), (129, 777, 768, 64),
-                                        (1000, 20000, 128, 256), (5, 300, 16, 256)])
+                                        (1000, 20000, 128, 256), (5, 300, 16, 256), (7, 20, 32, 256),
+                                        (40, 5, 64, 256)])
 @pytest.mark.parametrize("dtype", [K.KANN_BF16, K.KANN_F16])
 def test_tc_exact_integer_data_bit_exact(nq, nb, d, hi, dtype):
     rng = np.random.default_rng(nq + nb + d)
@@ -33,6 +34,23 @@ def test_tc_exact_integer_data_bit_exact(nq, nb, d, hi, dtype):
     gi, gd = K.kann_exact_knn(to16(Q, dtype), to16(X, dtype), k, K.KANN_L2, dtype=dtype)
     torch.cuda.synchronize()
     oi, od = O.exact_dense(X, Q, k, O.L2)
+    assert np.array_equal(gi.cpu().numpy(), oi)
+    assert np.array_equal(gd.cpu().numpy().astype(np.float64), od)
+
+
+@pytest.mark.parametrize("k", [1, 10, 32])
+@pytest.mark.parametrize("metric", [K.KANN_L2, K.KANN_IP])
+def test_tc_exact_ties_keep_lowest_ids(k, metric):
+    # a base of a few distinct rows repeated: every query's k-th distance is
+    # shared by hundreds of rows, and the (distance, id) order keeps the
+    # lowest ids -- the starting threshold of each scan must let them all in
+    rng = np.random.default_rng(11 + k)
+    proto = rng.integers(0, 64, (3, 64)).astype(np.float32)
+    X = proto[rng.integers(0, 3, 6000)]
+    Q = rng.integers(0, 64, (70, 64)).astype(np.float32)
+    gi, gd = K.kann_exact_knn(to16(Q, K.KANN_BF16), to16(X, K.KANN_BF16), k, metric, dtype=K.KANN_BF16)
+    torch.cuda.synchronize()
+    oi, od = O.exact_dense(X, Q, k, metric)
     assert np.array_equal(gi.cpu().numpy(), oi)
     assert np.array_equal(gd.cpu().numpy().astype(np.float64), od)
 

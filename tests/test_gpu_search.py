@@ -107,6 +107,62 @@ def test_integer_data_bit_exact(int_small, dtype):
         assert np.array_equal(gd.astype(np.float64), od)
 
 
+# Row widths that tile the lanes exactly (compile-time lane mapping) and widths
+# that do not (general kernels), plus lane-mapping overrides at d = 128: on
+# integer data every form must reproduce the oracle bit for bit.
+@pytest.fixture(scope="module")
+def int_dims():
+    out = {}
+    for d in (48, 64, 96, 256):
+        X, Q = G.integer_mixture(4000, 120, d=d, clusters=16, sigma=20.0, seed=40 + d)
+        out[d] = (X, Q, O.build_dense(X, O.L2, 16, 64, 40 + d))
+    return out
+
+
+@pytest.mark.parametrize("d", [48, 64, 96, 256])
+@pytest.mark.parametrize("dtype", [K.KANN_F32, K.KANN_F16, K.KANN_BF16])
+def test_integer_bit_exact_across_row_widths(int_dims, d, dtype):
+    X, Q, g = int_dims[d]
+    idx, _, _ = upload(g.arrays(), X, dtype=dtype)
+    oi, od, _ = O.search_dense(g, X, Q, 10, 48, O.L2)
+    gi, gd = search(idx, Q, 10, 48)
+    assert np.array_equal(gi, oi)
+    assert np.array_equal(gd.astype(np.float64), od)
+
+
+@pytest.mark.parametrize("dtype,lpr", [(K.KANN_F16, 4), (K.KANN_F16, 16), (K.KANN_F16, 32), (K.KANN_F32, 4),
+                                       (K.KANN_F32, 16), (K.KANN_BF16, 16)])
+def test_lane_mapping_overrides_bit_exact(int_small, dtype, lpr):
+    X, Q, g = int_small
+    idx, _, _ = upload(g.arrays(), X, dtype=dtype)
+    oi, od, _ = O.search_dense(g, X, Q, 10, 64, O.L2)
+    gi, gd = search(idx, Q, 10, 64, lanes_per_row=lpr)
+    assert np.array_equal(gi, oi)
+    assert np.array_equal(gd.astype(np.float64), od)
+
+
+@pytest.mark.parametrize("dtype", [K.KANN_F16, K.KANN_BF16])
+@pytest.mark.parametrize("d", [64, 128, 256])
+def test_lean_form_bit_exact(int_dims, int_small, dtype, d):
+    X, Q, g = int_small if d == 128 else int_dims[d]
+    idx, _, _ = upload(g.arrays(), X, dtype=dtype)
+    oi, od, _ = O.search_dense(g, X, Q, 10, 48, O.L2)
+    gi, gd = search(idx, Q, 10, 48, lean=1)
+    assert np.array_equal(gi, oi)
+    assert np.array_equal(gd.astype(np.float64), od)
+
+
+@pytest.mark.parametrize("d", [64, 96, 256])
+def test_e4m3_parity_across_row_widths(int_dims, d):
+    X, Q, g = int_dims[d]
+    idx, codes, scale = upload(g.arrays(), X, dtype=K.KANN_E4M3)
+    c, s = codes.cpu().numpy(), scale.cpu().numpy()
+    oi, od, _ = O.search_dense(g, c, Q, 10, 48, O.L2, dtype=O.DT_E4M3, scale=s)
+    gi, gd = search(idx, Q, 10, 48)
+    assert id_set_match_fraction(gi, oi) >= 0.99
+    check_dists(c, Q, gi, gd, O.L2, dtype=O.DT_E4M3, scale=s)
+
+
 def test_forgetful_table_changes_nothing(int_small):
     X, Q, g = int_small
     idx, _, _ = upload(g.arrays(), X)

@@ -187,16 +187,17 @@ struct DenseBackend {
             Fmt<DT>::unpack(buf[u][c], x);
 #pragma unroll
             for (int e = 0; e < EPC; ++e) {
-              const float xv = (DT == KANN_E4M3) ? x[e] * sc[u] : x[e];
               if (MET == KANN_L2) {
-                const float t = qr[c][e] - xv;
+                // E4M3: q - s x in one rounding
+                const float t = (DT == KANN_E4M3) ? fmaf(-x[e], sc[u], qr[c][e]) : qr[c][e] - x[e];
                 acc = fmaf(t, t, acc);
               } else {
-                acc = fmaf(qr[c][e], xv, acc);
+                acc = fmaf(qr[c][e], x[e], acc);  // E4M3: the row's scale is applied once below
               }
             }
           }
         }
+        if (DT == KANN_E4M3 && MET != KANN_L2) acc *= sc[u];
         for (int o = lpr >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
         if (sub == 0 && r < cnt) ck[r] = make_key(MET == KANN_L2 ? acc : -acc, (uint32_t)cid[r]);
       }
@@ -428,6 +429,12 @@ __device__ __forceinline__ void rerank_dists(const unsigned char* rr, int64_t st
 // query).  Returns the number of re-ranked entries now at the front of W.
 __device__ __noinline__ int rerank_phase(const unsigned char* rr, int rr_dtype, int64_t stride, int nchunks, int lpr,
                                          int metric, const float* q, int R, u64* W, u64* ck, int* cid, int lane) {
+  // ask L2 for every re-rank row at once, so that the chunk-by-chunk loads
+  // below wait for L2 rather than for DRAM
+  for (int j = lane; j < R; j += 32) {
+    const unsigned char* row = rr + (int64_t)key_id(W[j]) * stride;
+    for (int off = 0; off < nchunks * 16; off += 128) asm volatile("prefetch.global.L2 [%0];" ::"l"(row + off));
+  }
   for (int b = 0; b < R; b += 64) {
     const int cb = min(64, R - b);
     for (int j = lane; j < cb; j += 32) cid[j] = (int)key_id(W[b + j]);

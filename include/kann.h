@@ -191,6 +191,18 @@ int kann_search_batch(const kann_index_t* idx, const float* d_queries, int n, co
                       const int32_t* d_ef, int kmax, int efmax, int32_t* d_ids, float* d_dists,
                       const kann_search_opts* opts, void* stream);
 
+/* Device bytes a batch of n queries (k <= kmax, ef <= efmax) needs besides
+ * the index, for admission by device memory: the caller's query rows (n * d
+ * FP32; for a sparse index only the CSR offsets, (n + 1) * 8 -- term and
+ * weight bytes come on top), per-query k and ef words (8 n), the outputs
+ * (n * kmax * 8), per-query status words (4 n) and the persistent launch's
+ * two counters (8).  The search itself allocates no device memory: beam,
+ * candidates and visited table live in shared memory.  Returns 0 when no
+ * search with these settings can run (null index, n < 0, kmax < 1,
+ * max(efmax, kmax) > KANN_MAX_EF, or a per-warp shared-memory need above the
+ * device's limit). */
+size_t kann_search_workspace_bytes(const kann_index_t* idx, int n, int kmax, int efmax);
+
 /* Sparse-query search over a sparse index: queries in CSR (d_q_indptr [n+1]
  * int64, d_q_terms uint16 sorted unique per row, d_q_weights FP32). */
 int kann_search_sparse(const kann_index_t* idx, const int64_t* d_q_indptr, const uint16_t* d_q_terms,

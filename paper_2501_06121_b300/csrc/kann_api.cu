@@ -394,6 +394,22 @@ int kann_search_batch(const kann_index_t* idx, const float* d_queries, int n, co
   return KANN_EINVAL;
 }
 
+size_t kann_search_workspace_bytes(const kann_index_t* idx, int n, int kmax, int efmax) {
+  if (!idx || n < 0 || kmax < 1) return 0;
+  const int efmax_eff = efmax > kmax ? efmax : kmax;
+  if (efmax_eff > KANN_MAX_EF) return 0;
+  int efcap = 32;
+  while (efcap < efmax_eff) efcap <<= 1;
+  const int hbits = default_hbits(efmax_eff);
+  int smem = search_warp_smem(efcap, hbits);
+  if (idx->kind == 1) smem = search_warp_smem_pq(efcap, hbits, idx->pq.m);
+  if (idx->kind == 2) smem = search_warp_smem_sparse(efcap, hbits);
+  if (smem > max_optin_smem()) return 0;
+  const int d = idx->kind == 1 ? idx->pq.m * idx->pq.dsub : idx->v.d;
+  const size_t q = idx->kind == 2 ? (size_t)(n + 1) * 8 : (size_t)n * (size_t)d * 4;
+  return q + (size_t)n * 8 + (size_t)n * (size_t)kmax * 8 + (size_t)n * 4 + 8;
+}
+
 int kann_search_sparse(const kann_index_t* idx, const int64_t* d_q_indptr, const uint16_t* d_q_terms,
                        const float* d_q_weights, int n, int k, int ef, int32_t* d_ids, float* d_dists,
                        const kann_search_opts* opts, void* stream) {

@@ -83,6 +83,7 @@ def _lib():
             "kann_search_ex": (I, [P, P, I, I, I, P, P, P, P]),
             "kann_search_batch": (I, [P, P, I, P, P, I, I, P, P, P, P]),
             "kann_search_sparse": (I, [P, P, P, P, I, I, I, P, P, P, P]),
+            "kann_search_workspace_bytes": (SZ, [P, I, I, I]),
             "kann_exact_knn": (I, [P, P, I, I64, I, I, I, I, P, P, P, SZ, P]),
             "kann_exact_knn_workspace_bytes": (SZ, [I, I64, I, I, I]),
             "kann_quantize": (I, [P, I64, I, I, P, P, P]),
@@ -249,6 +250,13 @@ def kann_search_batch(index, queries, k, ef, kmax=None, efmax=None, ids=None, di
     _check("kann_search_batch", _lib().kann_search_batch(index.handle, _dev(queries), n, _dev(k), _dev(ef), kmax, efmax,
                                                          _dev(ids), _dev(dists), ctypes.byref(o), _stream(stream)))
     return ids, dists
+
+
+def kann_search_workspace_bytes(index, n, kmax, efmax):
+    """Device bytes a batch of n queries (k <= kmax, ef <= efmax) needs besides
+    the index (queries, k/ef words, outputs, status, counters); 0 if no search
+    with these settings can run."""
+    return int(_lib().kann_search_workspace_bytes(index.handle, n, kmax, efmax))
 
 
 def kann_search_sparse(index, q_indptr, q_terms, q_weights, k, ef, ids=None, dists=None, stream=None, **opts):

@@ -68,7 +68,7 @@ class _Slot:
         self.stream.synchronize()
 
     def bytes(self):
-        return self.cap * (self.d * 4 + 8 + self.kmax * 8) + 8
+        return K.kann_search_workspace_bytes(self.index, self.cap, self.kmax, self.efmax)
 
     def submit(self, reqs):
         n = len(reqs)
@@ -108,7 +108,10 @@ class SearchServer:
         self.slots = collections.OrderedDict()
         for name, spec in indices.items():
             cap = slot_capacity
-            per = lambda c: c * (spec["d"] * 4 + 8 + spec["kmax"] * 8) + 8
+            per = lambda c: K.kann_search_workspace_bytes(spec["index"], c, spec["kmax"], spec["efmax"])
+            if per(cap) == 0:
+                raise ValueError("index %r cannot run a search with kmax=%d efmax=%d" % (name, spec["kmax"],
+                                                                                        spec["efmax"]))
             while cap > 16 and per(cap) * slots_per_index * len(indices) > memory_budget:
                 cap //= 2
             self.slots[name] = [_Slot(spec["index"], spec["d"], spec["kmax"], spec["efmax"], cap, device,

@@ -115,3 +115,22 @@ def test_autotuner_returns_result_preserving_settings(two_indices, tmp_path):
     torch.cuda.synchronize()
     assert torch.equal(a_i, b_i) and torch.equal(a_d, b_d)
     assert A.tune(idx, Qd, 10, 64, reps=2, cache_path=cache) == opts  # served from the cache
+
+
+def test_admission_bytes_follow_the_settings(two_indices):
+    idx_a, Qa, _ = two_indices["a"]
+    idx_b, _, _ = two_indices["b"]
+    assert K.kann_search_workspace_bytes(idx_a, 100, 10, 64) == 100 * 128 * 4 + 100 * 8 + 100 * 10 * 8 + 100 * 4 + 8
+    assert K.kann_search_workspace_bytes(idx_b, 7, 100, 512) == 7 * 64 * 4 + 7 * 8 + 7 * 100 * 8 + 7 * 4 + 8
+    assert K.kann_search_workspace_bytes(idx_a, 0, 10, 64) == 8
+    assert K.kann_search_workspace_bytes(idx_a, 10, 10, K.KANN_MAX_EF + 1) == 0
+    assert K.kann_search_workspace_bytes(idx_a, 10, 0, 64) == 0
+    assert K.kann_search_workspace_bytes(idx_a, -1, 10, 64) == 0
+    # the server sizes its slots with it, halving the capacity until they fit the budget
+    spec = {"a": dict(index=idx_a, d=128, kmax=10, efmax=64)}
+    per_slot = K.kann_search_workspace_bytes(idx_a, 64, 10, 64)
+    srv = S.SearchServer(spec, slots_per_index=2, slot_capacity=256, memory_budget=2 * per_slot)
+    assert srv.device_bytes == 2 * per_slot
+    assert all(s.cap == 64 for s in srv.slots["a"])
+    with pytest.raises(ValueError):
+        S.SearchServer({"a": dict(index=idx_a, d=128, kmax=10, efmax=K.KANN_MAX_EF + 1)})

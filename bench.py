@@ -288,9 +288,13 @@ def run_pq768(args, n=None, concentration=None):
                 continue
             ms, (ids, _) = timed(lambda: K_.kann_search_ex(idx_pq, Qd, k, ef, rerank=100 if k <= 100 else -1))
             r = recall_at(ids.cpu().numpy(), gt100, k)
+            ms16, (ids16, _) = timed(lambda: K_.kann_search_ex(idx_pq, Qd, k, ef, rerank=100 if k <= 100 else -1,
+                                                               pq_lut_f16=1))
+            r16 = recall_at(ids16.cpu().numpy(), gt100, k)
             ms32, (ids32, _) = timed(lambda: K_.kann_search_ex(idx32, Qd, k, ef))
             r32 = recall_at(ids32.cpu().numpy(), gt100, k)
             rows.append({"k": k, "ef": ef, "pq_rerank100_qps": 1e4 / (ms / 1e3), "pq_rerank100_recall": r,
+                         "pq_f16table_rerank100_qps": 1e4 / (ms16 / 1e3), "pq_f16table_rerank100_recall": r16,
                          "fp32_qps": 1e4 / (ms32 / 1e3), "fp32_recall": r32})
             print(json.dumps(rows[-1]), flush=True)
     out = {"workload": "pq768", "n": n, "concentration": concentration,

@@ -155,7 +155,11 @@ typedef struct {
   int32_t lean;            /* dense rows of 2 chunks per lane: 1 = half the row batches in
                               flight for a 64-register budget (more warps per SM), -1 = off,
                               0 = automatic (off) */
-  int32_t reserved;
+  int32_t pq_lut_f16;      /* PQ index only: 1 = per-query table held in FP16 (entries scaled by
+                              the power of two that brings the largest |entry| to at most
+                              2^15, rounded to nearest; each row's FP32 sum scaled back): half
+                              the shared memory, so twice the queries per SM at m = 192.
+                              0 = FP32 table */
   uint32_t* d_status;      /* [n] per-query KANN_QSTAT_* bits, nullable */
   int32_t* d_counters;     /* [n][4] per-query counters, nullable: layer-0 distance
                               evaluations, layer-0 expansions, upper-layer distance

@@ -53,14 +53,15 @@ def lib():
             "orc_graph_import": [_i64, _i32, _i32, _i32, _i64, _p, _p, _p, _p],
             "orc_search_dense": [_p, _i32, _p, _p, _i32, _i32, _p, _i64, _i32, _i32, _i32, _i64, _i32,
                                  _p, _p, _p],
-            "orc_search_pq": [_p, _p, _p, _i32, _i32, _i32, _i32, _p, _i64, _i32, _i32, _i32, _i32, _p, _p, _p],
+            "orc_search_pq": [_p, _p, _p, _i32, _i32, _i32, _i32, _i32, _p, _i64, _i32, _i32, _i32, _i32, _p, _p,
+                              _p],
             "orc_search_sparse": [_p, _p, _p, _p, _p, _p, _p, _i64, _i32, _i32, _i32, _i32, _p, _p, _p],
             "orc_rerank_dense": [_i32, _p, _p, _i32, _i32, _p, _i64, _p, _i32, _i32, _p, _p],
             "orc_dist_dense": [_i32, _p, _p, _i32, _i32, _p, _i64, _p, _i32, _p],
             "orc_exact_dense": [_i32, _p, _p, _i64, _i32, _i32, _p, _i64, _i32, _i32, _p, _p],
             "orc_exact_sparse": [_p, _p, _p, _i64, _p, _p, _p, _i64, _i32, _i32, _p, _p],
             "orc_exact_pq": [_p, _p, _i64, _i32, _i32, _i32, _i32, _p, _i64, _i32, _p, _p],
-            "orc_pq_lut": [_p, _i32, _i32, _i32, _i32, _p, _p],
+            "orc_pq_lut": [_p, _i32, _i32, _i32, _i32, _i32, _p, _p],
             "orc_pq_encode": [_p, _i64, _i32, _i32, _i32, _p, _p],
             "orc_pq_reconstruct": [_p, _i64, _i32, _i32, _i32, _p, _p],
             "orc_pq_train": [_p, _i64, _i32, _i32, _i32, _i32, _u64, _p, _p],
@@ -212,7 +213,10 @@ def search_dense(g, data, queries, k, ef, metric, dtype=DT_F32, scale=None, form
     return ids, dists, cnt
 
 
-def search_pq(g, codes, codebooks, queries, k, ef, metric, form=FORM_FLAGS, nthreads=0):
+def search_pq(g, codes, codebooks, queries, k, ef, metric, form=FORM_FLAGS, nthreads=0, lut_f16=False):
+    """ADC search; lut_f16: the per-query table held in FP16 with a power-of-two
+    scale (each entry scaled so the largest |entry| is at most 2^15, rounded
+    to nearest, scaled back)."""
     codes = _c(codes, np.uint8)
     codebooks = _c(codebooks, np.float32)
     queries = _c(queries, np.float32)
@@ -221,8 +225,8 @@ def search_pq(g, codes, codebooks, queries, k, ef, metric, form=FORM_FLAGS, nthr
     ids = np.empty((nq, k), np.int32)
     dists = np.empty((nq, k), np.float64)
     cnt = np.empty((nq, 4), np.int64)
-    lib().orc_search_pq(g.h, _ptr(codes), _ptr(codebooks), m, ksub, dsub, metric, _ptr(queries), nq, k, ef,
-                        form, nthreads, _ptr(ids), _ptr(dists), _ptr(cnt))
+    lib().orc_search_pq(g.h, _ptr(codes), _ptr(codebooks), m, ksub, dsub, metric, int(bool(lut_f16)), _ptr(queries),
+                        nq, k, ef, form, nthreads, _ptr(ids), _ptr(dists), _ptr(cnt))
     return ids, dists, cnt
 
 
@@ -329,10 +333,10 @@ def pq_reconstruct(codes, codebooks):
     return out
 
 
-def pq_lut(codebooks, q, metric):
+def pq_lut(codebooks, q, metric, lut_f16=False):
     codebooks = _c(codebooks, np.float32)
     q = _c(q, np.float32)
     m, ksub, dsub = codebooks.shape
     lut = np.empty((m, ksub), np.float64)
-    lib().orc_pq_lut(_ptr(codebooks), m, ksub, dsub, metric, _ptr(q), _ptr(lut))
+    lib().orc_pq_lut(_ptr(codebooks), m, ksub, dsub, metric, int(bool(lut_f16)), _ptr(q), _ptr(lut))
     return lut

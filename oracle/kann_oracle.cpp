@@ -225,15 +225,21 @@ struct DenseSpace : Space {
 // Product-quantized vectors: asymmetric distance through a per-query table
 // (Jegou et al.): LUT[j][c] = partial distance of query sub-vector j to
 // centroid c of subspace j; d(q, x) = sum_j LUT[j][code_j(x)].
+// With lut_f16 the table is held at reduced precision (a reading: the paper
+// does not fix the table's precision): every entry is scaled by 2^-e, where
+// 2^e is the power of two that brings the largest |entry| to at most 2^15,
+// rounded to FP16 (nearest, ties to even), and scaled back; the scaling is
+// exact, so only the FP16 rounding of each entry remains.
 struct PQSpace : Space {
   int m, ksub, dsub, metric;
   const uint8_t* codes;
   const float* codebooks;  // [m][ksub][dsub]
   std::vector<double> lut;
+  bool lut_f16;
 
-  PQSpace(const uint8_t* codes_, const float* cb_, int m_, int ksub_, int dsub_, int metric_)
+  PQSpace(const uint8_t* codes_, const float* cb_, int m_, int ksub_, int dsub_, int metric_, bool f16 = false)
       : m(m_), ksub(ksub_), dsub(dsub_), metric(metric_), codes(codes_), codebooks(cb_),
-        lut((size_t)m_ * ksub_) {}
+        lut((size_t)m_ * ksub_), lut_f16(f16) {}
 
   void set_query(const float* qv) {
     for (int j = 0; j < m; ++j)
@@ -247,6 +253,14 @@ struct PQSpace : Space {
         }
         lut[(size_t)j * ksub + c] = s;
       }
+    if (lut_f16) {
+      double mx = 0.0;
+      for (double v : lut) mx = std::fmax(mx, std::fabs(v));
+      int E = 0;
+      if (mx > 0.0) std::frexp(mx, &E);  // mx = f * 2^E, f in [0.5, 1)
+      const int e = E - 15;
+      for (double& v : lut) v = std::ldexp(round_to_format(std::ldexp(v, -e), 11, -14, 65504.0, false), e);
+    }
   }
   void set_query_item(int64_t) override {}
   double qdist(int64_t i) const override {
@@ -720,12 +734,12 @@ void orc_search_dense(const void* gp, int dtype, const void* data, const float* 
 }
 
 void orc_search_pq(const void* gp, const uint8_t* codes, const float* codebooks, int m, int ksub, int dsub,
-                   int metric, const float* queries, int64_t nq, int k, int ef, int form, int nthreads,
-                   int32_t* ids, double* dists, int64_t* counters) {
+                   int metric, int lut_f16, const float* queries, int64_t nq, int k, int ef, int form,
+                   int nthreads, int32_t* ids, double* dists, int64_t* counters) {
   const Graph& g = *(const Graph*)gp;
 #pragma omp parallel num_threads(threads_or_default(nthreads))
   {
-    PQSpace sp(codes, codebooks, m, ksub, dsub, metric);
+    PQSpace sp(codes, codebooks, m, ksub, dsub, metric, lut_f16 != 0);
 #pragma omp for schedule(dynamic, 1)
     for (int64_t qi = 0; qi < nq; ++qi) {
       sp.set_query(queries + (size_t)qi * m * dsub);
@@ -836,8 +850,9 @@ void orc_exact_pq(const uint8_t* codes, const float* codebooks, int64_t n, int m
 
 // ----------------------------- PQ ------------------------------------------
 // Per-query ADC table, [m][ksub] FP64.
-void orc_pq_lut(const float* codebooks, int m, int ksub, int dsub, int metric, const float* q, double* lut) {
-  PQSpace sp(nullptr, codebooks, m, ksub, dsub, metric);
+void orc_pq_lut(const float* codebooks, int m, int ksub, int dsub, int metric, int lut_f16, const float* q,
+                double* lut) {
+  PQSpace sp(nullptr, codebooks, m, ksub, dsub, metric, lut_f16 != 0);
   sp.set_query(q);
   std::memcpy(lut, sp.lut.data(), sizeof(double) * (size_t)m * ksub);
 }

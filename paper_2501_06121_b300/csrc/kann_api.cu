@@ -154,6 +154,8 @@ int fill_search_args(const kann_index_t* idx, const float* d_q, int n, int k, in
     a.lpr_override = l;
     if (opts->lean < -1 || opts->lean > 1) return KANN_EINVAL;
     a.lean = opts->lean > 0 ? 1 : 0;
+    if (opts->pq_lut_f16 < 0 || opts->pq_lut_f16 > 1) return KANN_EINVAL;
+    a.lut16 = opts->pq_lut_f16;
     R = opts->rerank;
     if (R < -1) return KANN_EINVAL;
     a.work_counter = opts->d_work_counter;
@@ -215,10 +217,10 @@ int run_pq(const kann_index_t* idx, SearchArgs& a, int wpb, void* stream) {
   if ((a.nchunks + a.lpr - 1) / a.lpr > 4) return KANN_EINVAL;
   if (a.nq > 0 && (!a.q || !aligned16(a.q))) return KANN_EINVAL;
   const int optin = max_optin_smem();
-  a.warp_smem = search_warp_smem_pq(a.efcap, a.hbits, pq.m);
+  a.warp_smem = search_warp_smem_pq(a.efcap, a.hbits, pq.m, a.lut16 != 0);
   while (a.warp_smem > optin && a.hbits > 8) {
     --a.hbits;
-    a.warp_smem = search_warp_smem_pq(a.efcap, a.hbits, pq.m);
+    a.warp_smem = search_warp_smem_pq(a.efcap, a.hbits, pq.m, a.lut16 != 0);
   }
   if (a.warp_smem > optin) return KANN_ENOMEM;
   while (wpb > 1 && wpb * a.warp_smem > optin) --wpb;

@@ -45,6 +45,7 @@ struct SearchArgs {
   int* work_counter;     // persistent mode: next query index (zeroed before launch), or null
   const int32_t* d_n;    // persistent mode: device-side query count (<= nq), or null
   int lean;              // dense: half the rows in flight, 64-register budget
+  int lut16;             // PQ: per-query table in FP16 with a power-of-two scale
   int efcap;       // W capacity (power of two >= efmax, >= 32)
   int warp_smem;   // bytes of shared memory per warp
 };
@@ -78,7 +79,7 @@ SearchKernelFn pick_search_e4m3(int cplt, bool lean, int metric, int lpr_exact);
 
 // Per-warp shared memory needed by a dense search with these settings.
 int search_warp_smem(int efcap, int hbits);
-int search_warp_smem_pq(int efcap, int hbits, int m);
+int search_warp_smem_pq(int efcap, int hbits, int m, bool lut16 = false);
 int search_warp_smem_sparse(int efcap, int hbits);
 
 // Launchers (kann_search.cu); return a cudaError_t.

@@ -67,7 +67,9 @@ int launch_search_dense(const SearchArgs& a, int dtype, int wpb, void* stream) {
   return (int)cudaGetLastError();
 }
 
-int search_warp_smem_pq(int efcap, int hbits, int m) { return search_warp_smem(efcap, hbits) + m * 256 * 4; }
+int search_warp_smem_pq(int efcap, int hbits, int m, bool lut16) {
+  return search_warp_smem(efcap, hbits) + m * 256 * (lut16 ? 2 : 4);
+}
 
 int search_warp_smem_sparse(int efcap, int hbits) { return search_warp_smem(efcap, hbits) + SP_QH * 8; }
 
@@ -75,9 +77,9 @@ int launch_search_pq(const SearchArgs& a, int wpb, void* stream) {
   if (a.nq == 0) return 0;
   const int cplt = pow2_at_least((a.nchunks + a.lpr - 1) / a.lpr);
   SearchKernelFn fn = nullptr;
-  if (cplt == 1) fn = search_pq_kernel<1>;
-  if (cplt == 2) fn = search_pq_kernel<2>;
-  if (cplt == 4) fn = search_pq_kernel<4>;
+  if (cplt == 1) fn = a.lut16 ? search_pq_kernel<1, true> : search_pq_kernel<1, false>;
+  if (cplt == 2) fn = a.lut16 ? search_pq_kernel<2, true> : search_pq_kernel<2, false>;
+  if (cplt == 4) fn = a.lut16 ? search_pq_kernel<4, true> : search_pq_kernel<4, false>;
   if (!fn) return (int)cudaErrorInvalidValue;
   const size_t smem = (size_t)wpb * a.warp_smem;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -29,6 +29,8 @@
 // improves once W is full; the search therefore returns the same W as with an
 // exact visited set.  Forgotten ids cost only a repeated distance.
 #pragma once
+#include <type_traits>
+
 #include "kann_device.cuh"
 #include "kann_internal.h"
 
@@ -212,31 +214,52 @@ struct DenseBackend {
 // in shared memory, then d(q, x) = sum_j LUT[j][code_j(x)].  A row is the m
 // code bytes of an item; lanes own 16-byte chunks of it exactly as in the
 // dense back-end, summing their lookups in byte order.
+//
+// L16: the table is held in FP16 (half the shared memory, so twice the
+// queries per SM at m = 192): entries are scaled by 2^-e, with 2^e the power
+// of two that brings the largest |entry| to at most 2^15, rounded to nearest,
+// and the FP32 sum of a row's lookups is scaled back by 2^e (exact).
 // ---------------------------------------------------------------------------
-template <int CPL>
+template <int CPL, bool L16>
 struct PQBackend {
   static constexpr int U = (8 / CPL) > 0 ? (8 / CPL) : 1;
-  float* lut;
+  typedef typename std::conditional<L16, __half, float>::type LutT;
+  LutT* lut;
+  float scale;  // 2^e for the FP16 table, 1 otherwise
+
+  __device__ __forceinline__ static float entry(const SearchArgs& a, const float* q, int e) {
+    const int j = e >> 8, dsub = a.pq_dsub;
+    const float* C = a.codebooks + (size_t)e * dsub;
+    const float* qq = q + j * dsub;
+    float s = 0.f;
+    for (int t = 0; t < dsub; ++t) {
+      const float cv = __ldg(C + t), qv = __ldg(qq + t);
+      if (a.metric == KANN_L2) {
+        const float u = qv - cv;
+        s = fmaf(u, u, s);
+      } else {
+        s = fmaf(qv, cv, s);
+      }
+    }
+    return a.metric == KANN_L2 ? s : -s;
+  }
 
   __device__ __forceinline__ void init(const SearchArgs& a, int qi, int lane, unsigned char* extra) {
-    lut = reinterpret_cast<float*>(extra);
-    const int m = a.pq_m, dsub = a.pq_dsub;
-    const float* q = a.q + (size_t)qi * m * dsub;
-    for (int e = lane; e < m * 256; e += 32) {
-      const int j = e >> 8;
-      const float* C = a.codebooks + (size_t)e * dsub;
-      const float* qq = q + j * dsub;
-      float s = 0.f;
-      for (int t = 0; t < dsub; ++t) {
-        const float cv = __ldg(C + t), qv = __ldg(qq + t);
-        if (a.metric == KANN_L2) {
-          const float u = qv - cv;
-          s = fmaf(u, u, s);
-        } else {
-          s = fmaf(qv, cv, s);
-        }
-      }
-      lut[e] = a.metric == KANN_L2 ? s : -s;
+    lut = reinterpret_cast<LutT*>(extra);
+    const int m = a.pq_m;
+    const float* q = a.q + (size_t)qi * m * a.pq_dsub;
+    scale = 1.f;
+    if (!L16) {
+      for (int e = lane; e < m * 256; e += 32) lut[e] = entry(a, q, e);
+    } else {
+      float mx = 0.f;
+      for (int e = lane; e < m * 256; e += 32) mx = fmaxf(mx, fabsf(entry(a, q, e)));
+      for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(FULL, mx, o));
+      int E = 0;
+      if (mx > 0.f) frexpf(mx, &E);  // mx = f * 2^E, f in [0.5, 1)
+      const int sh = E - 15;
+      for (int e = lane; e < m * 256; e += 32) lut[e] = __float2half_rn(ldexpf(entry(a, q, e), -sh));
+      scale = ldexpf(1.f, sh);
     }
     __syncwarp();
   }
@@ -267,12 +290,17 @@ struct PQBackend {
           const int ch = sub + c * lpr;
           if (ch < a.nchunks) {
             const uint32_t w[4] = {buf[u][c].x, buf[u][c].y, buf[u][c].z, buf[u][c].w};
-            const float* L = lut + (size_t)ch * 16 * 256;
+            const LutT* L = lut + (size_t)ch * 16 * 256;
 #pragma unroll
-            for (int b = 0; b < 16; ++b) acc += L[b * 256 + ((w[b >> 2] >> (8 * (b & 3))) & 0xffu)];
+            for (int b = 0; b < 16; ++b) {
+              const LutT v = L[b * 256 + ((w[b >> 2] >> (8 * (b & 3))) & 0xffu)];
+              if constexpr (L16) acc += __half2float(v);
+              else acc += v;
+            }
           }
         }
         for (int o = lpr >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
+        if (L16) acc *= scale;
         if (sub == 0 && r < cnt) ck[r] = make_key(acc, (uint32_t)cid[r]);
       }
     }
@@ -788,9 +816,9 @@ __global__ void __launch_bounds__(128, MinBlocks<DT, CPLT, LEAN>::value) search_
   run_queries(a, be);
 }
 
-template <int CPLT>
+template <int CPLT, bool L16>
 __global__ void __launch_bounds__(128, 1) search_pq_kernel(const SearchArgs a) {
-  PQBackend<CPLT> be;
+  PQBackend<CPLT, L16> be;
   run_queries(a, be);
 }
 

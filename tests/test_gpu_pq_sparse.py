@@ -56,6 +56,38 @@ def test_pq_parity(pq_setup, metric):
     assert np.all(np.abs(gd - ref) <= 1e-5 * np.maximum(np.abs(ref), mag) + 1e-30)
 
 
+@pytest.mark.parametrize("metric", [K.KANN_IP, K.KANN_L2])
+def test_pq_fp16_table_parity(pq_setup, metric):
+    # the FP16 table (power-of-two scale, entries rounded to nearest) against
+    # the oracle's search with the same reading of the table
+    X, Q, g, cb, codes = pq_setup
+    idx = K.kann_index_upload(K.graph_to_device(g.arrays()),
+                              pq=dict(codes=dev(codes), codebooks=dev(cb), metric=metric))
+    oi, od, _ = O.search_pq(g, codes, cb, Q, 10, 64, metric, lut_f16=True)
+    gi, gd = K.kann_search_ex(idx, dev(Q), 10, 64, pq_lut_f16=1)
+    torch.cuda.synchronize()
+    gi, gd = gi.cpu().numpy(), gd.cpu().numpy()
+    assert id_set_match_fraction(gi, oi) >= 0.999
+    ref = np.zeros(gi.shape)
+    mag = np.zeros(gi.shape)
+    for qi in range(len(Q)):
+        lut = O.pq_lut(cb, Q[qi], metric, lut_f16=True)
+        terms = lut[np.arange(16)[None, :], codes[gi[qi]].astype(int)]
+        ref[qi] = terms.sum(1)
+        mag[qi] = np.abs(terms).sum(1)
+    # FP32 arithmetic as in the FP32-table contract, plus: the GPU rounds its
+    # FP32 entry and the oracle its FP64 entry to FP16, so an entry that lies
+    # next to a rounding boundary may land one FP16 step (2^-10 relative, or
+    # 2^-9 if the scale's power of two flips too) away
+    tol = 1e-5 * np.maximum(np.abs(ref), mag) + 2.0 ** -9 * mag + 1e-30
+    assert np.all(np.abs(gd - ref) <= tol)
+    assert np.mean(np.abs(gd - ref) <= 1e-5 * np.maximum(np.abs(ref), mag) + 1e-30) >= 0.99
+    # and the search it drives stays close to the FP32-table search
+    fi, _ = K.kann_search(idx, dev(Q), 10, 64)
+    torch.cuda.synchronize()
+    assert id_set_match_fraction(gi, fi.cpu().numpy()) >= 0.95
+
+
 def test_pq_rerank(pq_setup):
     X, Q, g, cb, codes = pq_setup
     Xd = dev(X)

@@ -71,3 +71,42 @@ def test_encode_picks_nearest_and_lowest_on_ties():
     codes = O.pq_encode(X, cb)
     # [0.5, 0.5] is equidistant from centroids 0, 1 and 2 -> lowest index
     assert codes[:, 0].tolist() == [0, 1, 0, 3, 0]
+
+
+def test_fp16_table_is_the_scaled_half_rounding_of_the_fp64_table():
+    # independent restatement with numpy: scale by the power of two that puts
+    # the largest |entry| in [2^14, 2^15), round to float16 (nearest, ties to
+    # even), scale back
+    X, Q = _data(d=32, seed=7)
+    for metric in (O.L2, O.IP):
+        cb, _ = O.pq_train(X, m=8, ksub=64, iters=4, seed=8)
+        for q in Q[:6]:
+            t64 = O.pq_lut(cb, q, metric)
+            t16 = O.pq_lut(cb, q, metric, lut_f16=True)
+            mx = np.abs(t64).max()
+            e = int(np.floor(np.log2(mx))) + 1 - 15
+            ref = np.ldexp(np.ldexp(t64, -e).astype(np.float16).astype(np.float64), e)
+            assert np.array_equal(t16, ref)
+            assert 2.0 ** 14 <= np.abs(np.ldexp(t16, -e)).max() <= 2.0 ** 15
+            # half-ulp bound of the rounding
+            assert np.all(np.abs(t16 - t64) <= np.maximum(2.0 ** -11 * np.abs(t64), 2.0 ** (e - 25)))
+
+
+def test_fp16_table_is_exact_on_small_integer_tables():
+    # entries are small integers (after the exact power-of-two scaling they
+    # still have at most 11 significant bits): the FP16 table loses nothing,
+    # so the search equals the FP64-table search
+    rng = np.random.default_rng(9)
+    m, dsub = 4, 2
+    X = rng.integers(-6, 7, size=(800, m * dsub)).astype(np.float32)
+    cb, _ = O.pq_train(X, m=m, ksub=16, iters=6, seed=9)
+    cb = np.round(cb).astype(np.float32)
+    codes = O.pq_encode(X, cb)
+    Q = rng.integers(-6, 7, size=(25, m * dsub)).astype(np.float32)
+    for metric in (O.L2, O.IP):
+        for q in Q[:5]:
+            assert np.array_equal(O.pq_lut(cb, q, metric, lut_f16=True), O.pq_lut(cb, q, metric))
+        g = O.build_dense(X, metric, 8, 60, 10)
+        a = O.search_pq(g, codes, cb, Q, 10, 40, metric, lut_f16=True)
+        b = O.search_pq(g, codes, cb, Q, 10, 40, metric)
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])

@@ -9,8 +9,11 @@
 // One persistent CTA per SM walks work items (a tile of 128 queries x one
 // split of the base).  Roles inside a CTA (320 threads):
 //   warp 0      TMA producer: per base tile of 256 rows and per 64-element K
-//               chunk, loads the query chunk (128 x 64) and the base chunk
-//               (256 x 64), 128-byte swizzled, into a 4-stage ring;
+//               chunk, loads the base chunk (256 x 64), 128-byte swizzled,
+//               into a stage ring; for d <= 256 the item's 128 x d query block
+//               is loaded once per item and stays resident (the MMAs of every
+//               tile read it), otherwise each stage carries its query chunk
+//               (128 x 64) too;
 //   warp 1      allocates 512 TMEM columns (two 128 x 256 FP32 accumulators)
 //               and issues tcgen05.mma (M=128, N=256, K=16) from one lane;
 //               tcgen05.commit frees a ring stage when its MMAs are done and
@@ -45,7 +48,8 @@ namespace {
 constexpr int TC_M = 128;       // queries per work item (TMEM lanes)
 constexpr int TC_N = 256;       // base rows per tile (accumulator columns)
 constexpr int TC_K = 64;        // K elements per stage: one 128-byte swizzle row
-constexpr int TC_MAX_STAGES = 4;
+constexpr int TC_MAX_STAGES = 6;
+constexpr int TC_QRES_MAX_KCHUNKS = 4;  // resident query block up to d = 256
 constexpr int A_BYTES = TC_M * TC_K * 2;
 constexpr int B_BYTES = TC_N * TC_K * 2;
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
@@ -61,7 +65,10 @@ struct TcArgs {
   int d, metric, k, S, kchunks;
   int64_t per;          // base rows per split (a multiple of TC_N)
   int n_items;
-  int stages;           // ring depth (3 or 4, by shared memory left for the top-k lists)
+  int stages;           // ring depth (by shared memory left for the query block and the top-k lists)
+  int qres;             // 1: the item's query block is resident, stages hold base chunks only
+  int stage_bytes;      // B_BYTES (qres) or A_BYTES + B_BYTES
+  int qbytes;           // kchunks * A_BYTES (qres) or 0
   uint32_t idesc;
   const float* xnorm;   // [nb]
   const float* qnorm;   // [nq]
@@ -252,10 +259,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   // 1024-byte alignment for the swizzled stages
   unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int NS = a.stages;
-  unsigned char* stage_base = smem;
-  u64* bars = reinterpret_cast<u64*>(smem + NS * STAGE_BYTES);
-  // bars: full[NS], empty[NS], tfull[2], tempty[2]
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * TC_MAX_STAGES + 4);
+  unsigned char* qblock = smem;                 // resident query block (qres)
+  unsigned char* stage_base = smem + a.qbytes;
+  u64* bars = reinterpret_cast<u64*>(stage_base + NS * a.stage_bytes);
+  // bars: full[NS], empty[NS], tfull[2], tempty[2], qfull, qempty
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * TC_MAX_STAGES + 6);
   float* xn_s = reinterpret_cast<float*>(tmem_slot + 4);        // [8][128] per-warp tile norms
   float* list_d = xn_s + TC_EPI_WARPS * 128;                    // [2][128][k] top-k distances
   int* list_i = reinterpret_cast<int*>(list_d + 2 * TC_M * a.k); // [2][128][k] top-k ids
@@ -263,6 +271,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + TC_MAX_STAGES);
   const uint32_t tfull0 = smem_u32(bars + 2 * TC_MAX_STAGES), tempty0 = smem_u32(bars + 2 * TC_MAX_STAGES + 2);
+  const uint32_t qfull0 = smem_u32(bars + 2 * TC_MAX_STAGES + 4), qempty0 = smem_u32(bars + 2 * TC_MAX_STAGES + 5);
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < NS; ++s) {
@@ -273,6 +282,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       mbar_init(tfull0 + 8 * b, 1);
       mbar_init(tempty0 + 8 * b, TC_EPI_WARPS);
     }
+    mbar_init(qfull0, 1);
+    mbar_init(qempty0, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
@@ -289,21 +300,34 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   if (warp == 0) {
     // ---------------- TMA producer ----------------
     if (lane == 0) {
-      uint32_t it = 0;
+      uint32_t it = 0, iq = 0;
       bool ok = true;
       for (int item = blockIdx.x; item < a.n_items && ok; item += gridDim.x) {
         const int q0 = (item / a.S) * TC_M;
         const int64_t b_begin = (int64_t)(item % a.S) * a.per;
         const int64_t b_end = b_begin + a.per < a.nb ? b_begin + a.per : a.nb;
+        if (a.qres) {
+          // the previous item's MMAs must be done with the resident block
+          ok = mbar_wait(qempty0, (iq & 1u) ^ 1u, a.err);
+          if (!ok) break;
+          mbar_expect_tx(qfull0, (uint32_t)a.qbytes);
+          for (int kc = 0; kc < a.kchunks; ++kc)
+            tma_load_2d(smem_u32(qblock + kc * A_BYTES), &tmQ, kc * TC_K, q0, qfull0);
+          ++iq;
+        }
         for (int64_t b0 = b_begin; b0 < b_end && ok; b0 += TC_N) {
           for (int kc = 0; kc < a.kchunks && ok; ++kc, ++it) {
             const uint32_t s = it % NS, ph = (it / NS) & 1u;
             ok = mbar_wait(empty0 + 8 * s, ph ^ 1u, a.err);
             if (!ok) break;
-            const uint32_t sa = smem_u32(stage_base + s * STAGE_BYTES);
-            mbar_expect_tx(full0 + 8 * s, STAGE_BYTES);
-            tma_load_2d(sa, &tmQ, kc * TC_K, q0, full0 + 8 * s);
-            tma_load_2d(sa + A_BYTES, &tmX, kc * TC_K, (int)b0, full0 + 8 * s);
+            const uint32_t sa = smem_u32(stage_base + s * a.stage_bytes);
+            mbar_expect_tx(full0 + 8 * s, (uint32_t)a.stage_bytes);
+            if (a.qres) {
+              tma_load_2d(sa, &tmX, kc * TC_K, (int)b0, full0 + 8 * s);
+            } else {
+              tma_load_2d(sa, &tmQ, kc * TC_K, q0, full0 + 8 * s);
+              tma_load_2d(sa + A_BYTES, &tmX, kc * TC_K, (int)b0, full0 + 8 * s);
+            }
           }
         }
       }
@@ -311,11 +335,16 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   } else if (warp == 1) {
     // ---------------- MMA issuer (one lane) ----------------
     if (lane == 0) {
-      uint32_t it = 0, t = 0;
+      uint32_t it = 0, t = 0, iq = 0;
       bool ok = true;
       for (int item = blockIdx.x; item < a.n_items && ok; item += gridDim.x) {
         const int64_t b_begin = (int64_t)(item % a.S) * a.per;
         const int64_t b_end = b_begin + a.per < a.nb ? b_begin + a.per : a.nb;
+        if (a.qres) {
+          ok = mbar_wait(qfull0, iq & 1u, a.err);
+          if (!ok) break;
+          tc_fence_after();
+        }
         for (int64_t b0 = b_begin; b0 < b_end && ok; b0 += TC_N, ++t) {
           const uint32_t buf = t & 1u, use = t >> 1;
           ok = mbar_wait(tempty0 + 8 * buf, (use & 1u) ^ 1u, a.err);
@@ -327,14 +356,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             ok = mbar_wait(full0 + 8 * s, ph, a.err);
             if (!ok) break;
             tc_fence_after();
-            const uint32_t sa = smem_u32(stage_base + s * STAGE_BYTES);
+            const uint32_t sa = smem_u32(stage_base + s * a.stage_bytes);
+            const uint32_t qa = a.qres ? smem_u32(qblock + kc * A_BYTES) : sa;
+            const uint32_t xa = a.qres ? sa : sa + A_BYTES;
 #pragma unroll
             for (int kk = 0; kk < TC_K / 16; ++kk)
-              tc_mma(dt, smem_desc(sa + kk * 32), smem_desc(sa + A_BYTES + kk * 32), a.idesc, (kc | kk) != 0);
+              tc_mma(dt, smem_desc(qa + kk * 32), smem_desc(xa + kk * 32), a.idesc, (kc | kk) != 0);
             tc_commit(empty0 + 8 * s);
           }
           if (!ok) break;
           tc_commit(tfull0 + 8 * buf);
+        }
+        if (a.qres && ok) {
+          tc_commit(qempty0);  // the resident block is free once this item's MMAs are done
+          ++iq;
         }
       }
     }
@@ -653,13 +688,18 @@ int exact_tc_run(const void* Q, const void* X, int nq, int64_t nb, int d, int me
   a.out = part;
   a.err = err;
   // shared memory: alignment pad, stage ring, barriers, norms, top-k lists
-  const size_t fixed = 1024 + (2 * TC_MAX_STAGES + 4) * 8 + 16 + TC_EPI_WARPS * 128 * 4 + (size_t)2 * TC_M * k * 8;
+  const size_t fixed = 1024 + (2 * TC_MAX_STAGES + 6) * 8 + 16 + TC_EPI_WARPS * 128 * 4 + (size_t)2 * TC_M * k * 8;
   int optin = 0, dev = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  // resident query block when it and a ring of at least 3 base stages fit
+  a.qres = a.kchunks <= TC_QRES_MAX_KCHUNKS &&
+           fixed + (size_t)a.kchunks * A_BYTES + 3 * (size_t)B_BYTES <= (size_t)optin;
+  a.qbytes = a.qres ? a.kchunks * A_BYTES : 0;
+  a.stage_bytes = a.qres ? B_BYTES : STAGE_BYTES;
   a.stages = TC_MAX_STAGES;
-  while (a.stages > 2 && fixed + (size_t)a.stages * STAGE_BYTES > (size_t)optin) --a.stages;
-  const size_t smem = fixed + (size_t)a.stages * STAGE_BYTES;
+  while (a.stages > 2 && fixed + (size_t)a.qbytes + (size_t)a.stages * a.stage_bytes > (size_t)optin) --a.stages;
+  const size_t smem = fixed + (size_t)a.qbytes + (size_t)a.stages * a.stage_bytes;
   e = cudaFuncSetAttribute(exact_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return (int)e;
   const int grid = a.n_items < num_sms() ? a.n_items : num_sms();

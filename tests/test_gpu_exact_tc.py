@@ -24,7 +24,7 @@ def to16(a, dtype):
 
 @pytest.mark.parametrize("nq,nb,d,hi", [(300, 5000, 128, 256), (1, 1000, 64, 256), (129, 777, 768, 64),
                                         (1000, 20000, 128, 256), (5, 300, 16, 256), (7, 20, 32, 256),
-                                        (40, 5, 64, 256)])
+                                        (40, 5, 64, 256), (300, 5000, 256, 64), (200, 3000, 192, 64)])
 @pytest.mark.parametrize("dtype", [K.KANN_BF16, K.KANN_F16])
 def test_tc_exact_integer_data_bit_exact(nq, nb, d, hi, dtype):
     rng = np.random.default_rng(nq + nb + d)

@@ -41,6 +41,32 @@ def rank_info():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def shard_queries(rank, world, nq=N_QUERY, seed=SEED):
+    """Queries of rank `rank` in a `world`-rank run (weak scaling): slice `rank`
+    of one draw of world * nq queries, so the shards are disjoint; one rank gets
+    the headline query set."""
+    if world == 1:
+        return make_workload(nq=nq, seed=seed)[1]
+    return make_workload(n=1, nq=nq * world, seed=seed)[1][rank * nq:(rank + 1) * nq]
+
+
+def max_over_ranks(x, world, device=None):
+    """The largest of every rank's x (the job's time is its slowest rank's)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_qps(world, nq, steps, max_ms):
+    """Whole-job throughput: the queries all ranks processed over the slowest
+    rank's time."""
+    return world * nq * steps / (max_ms / 1e3)
+
+
 def make_workload(n=N_BASE, nq=N_QUERY, seed=SEED):
     from paper_2501_06121_b300 import datagen as G
     return G.integer_mixture(n, nq, d=DIM, clusters=256, sigma=20.0, seed=seed)
@@ -482,7 +508,7 @@ def main():
     # ---- inputs (untimed)
     X, Q = make_workload(seed=SEED)
     if world > 1:
-        Q = make_workload(n=1, nq=N_QUERY * world, seed=SEED)[1][rank * N_QUERY:(rank + 1) * N_QUERY]
+        Q = shard_queries(rank, world)
     t0 = time.time()
     if world > 1 and rank != 0:
         dist.barrier()
@@ -553,14 +579,11 @@ def main():
     w0 = time.time()
     total_ms, per = timed(idx16, -1, args.steps, args.warmup)
     clk = clocks.stop(w0 + 1e-3 * 0, time.time())
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms, world, dev)
     fp32_ms, _ = timed(idx32, 0, max(3, args.steps // 2), 2)
     fp32_ms /= max(3, args.steps // 2)
 
-    qps = world * N_QUERY * args.steps / (total_ms / 1e3)
+    qps = job_qps(world, N_QUERY, args.steps, total_ms)
     ms_step = total_ms / args.steps
     per_launch_s = ms_step / 1e3
     achieved = N_QUERY * bytes_per_q / per_launch_s / 1e9
@@ -598,11 +621,8 @@ def main():
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_qps = world * N_QUERY * args.steps / (e2e_ms / 1e3)
+    e2e_ms = max_over_ranks(e2e_ms, world, dev)
+    e2e_qps = job_qps(world, N_QUERY, args.steps, e2e_ms)
     final_recall = recall_at(ids_buf.cpu().numpy(), gt)
     # tie-aware recall: a returned id counts when its exact distance is within
     # the k-th ground-truth distance (equal distances are common on integer data)

@@ -218,11 +218,11 @@ int run_pq(const kann_index_t* idx, SearchArgs& a, int wpb, void* stream) {
   if (a.nq > 0 && (!a.q || !aligned16(a.q))) return KANN_EINVAL;
   const int optin = max_optin_smem();
   a.warp_smem = search_warp_smem_pq(a.efcap, a.hbits, pq.m, a.lut16 != 0);
-  while (a.warp_smem > optin && a.hbits > 8) {
+  while (a.warp_smem + PQ_TEAM_CTL_BYTES > optin && a.hbits > 8) {
     --a.hbits;
     a.warp_smem = search_warp_smem_pq(a.efcap, a.hbits, pq.m, a.lut16 != 0);
   }
-  if (a.warp_smem > optin) return KANN_ENOMEM;
+  if (a.warp_smem + PQ_TEAM_CTL_BYTES > optin) return KANN_ENOMEM;
   while (wpb > 1 && wpb * a.warp_smem > optin) --wpb;
   if (a.nq == 0) return KANN_OK;
   return check_cuda((cudaError_t)launch_search_pq(a, wpb, stream));
@@ -404,7 +404,7 @@ size_t kann_search_workspace_bytes(const kann_index_t* idx, int n, int kmax, int
   while (efcap < efmax_eff) efcap <<= 1;
   const int hbits = default_hbits(efmax_eff);
   int smem = search_warp_smem(efcap, hbits);
-  if (idx->kind == 1) smem = search_warp_smem_pq(efcap, hbits, idx->pq.m);
+  if (idx->kind == 1) smem = search_warp_smem_pq(efcap, hbits, idx->pq.m) + PQ_TEAM_CTL_BYTES;
   if (idx->kind == 2) smem = search_warp_smem_sparse(efcap, hbits);
   if (smem > max_optin_smem()) return 0;
   const int d = idx->kind == 1 ? idx->pq.m * idx->pq.dsub : idx->v.d;

@@ -80,6 +80,8 @@ SearchKernelFn pick_search_e4m3(int cplt, bool lean, int metric, int lpr_exact);
 // Per-warp shared memory needed by a dense search with these settings.
 int search_warp_smem(int efcap, int hbits);
 int search_warp_smem_pq(int efcap, int hbits, int m, bool lut16 = false);
+// Shared memory of a PQ search team's control block (after the query's region).
+constexpr int PQ_TEAM_CTL_BYTES = 64;
 int search_warp_smem_sparse(int efcap, int hbits);
 
 // Launchers (kann_search.cu); return a cudaError_t.

@@ -81,13 +81,23 @@ int launch_search_pq(const SearchArgs& a, int wpb, void* stream) {
   if (cplt == 2) fn = a.lut16 ? search_pq_kernel<2, true> : search_pq_kernel<2, false>;
   if (cplt == 4) fn = a.lut16 ? search_pq_kernel<4, true> : search_pq_kernel<4, false>;
   if (!fn) return (int)cudaErrorInvalidValue;
-  const size_t smem = (size_t)wpb * a.warp_smem;
+  (void)wpb;  // one query per CTA of PQ_TEAM warps
+  static_assert(sizeof(TeamCtl) <= PQ_TEAM_CTL_BYTES, "team control block");
+  const size_t smem = (size_t)a.warp_smem + PQ_TEAM_CTL_BYTES;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return (int)e;
-  const int grid = launch_grid(fn, a, wpb, smem);
+  int grid = a.nq;
+  if (a.work_counter != nullptr) {
+    int dev = 0, sms = 148, per_sm = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, PQ_TEAM * 32, smem) != cudaSuccess || per_sm < 1)
+      per_sm = 1;
+    grid = a.nq < sms * per_sm ? a.nq : sms * per_sm;
+  }
   int c = start_counter(a, (cudaStream_t)stream);
   if (c) return c;
-  fn<<<grid, wpb * 32, smem, (cudaStream_t)stream>>>(a);
+  fn<<<grid, PQ_TEAM * 32, smem, (cudaStream_t)stream>>>(a);
   return (int)cudaGetLastError();
 }
 

@@ -84,6 +84,43 @@ __device__ __forceinline__ int count_le(const int* A, int n, int x) {
   return lo;
 }
 
+// Shared memory of one warp: W[efcap] keys, candidate keys[64], candidate
+// ids[64], candidate W-ranks[64], then the visited table (1 << hbits words),
+// then back-end scratch.
+struct WarpSmem {
+  u64* W;
+  u64* ck;
+  int* cid;
+  int* clb;
+  uint32_t* H;
+  unsigned char* extra;
+  __device__ __forceinline__ WarpSmem(unsigned char* ws, int efcap, int hbits) {
+    W = reinterpret_cast<u64*>(ws);
+    ck = W + efcap;
+    cid = reinterpret_cast<int*>(ck + 64);
+    clb = cid + 64;
+    H = reinterpret_cast<uint32_t*>(clb + 64);
+    extra = reinterpret_cast<unsigned char*>(H + (1 << hbits));
+  }
+};
+
+enum { TEAM_DIST = 1, TEAM_RERANK = 2, TEAM_DONE = 3 };
+
+struct TeamCtl {
+  int cmd, cnt, qi, pad;
+  float wmax[8];
+};
+
+__device__ __forceinline__ void team_bar(int T) { asm volatile("bar.sync 1, %0;" ::"r"(T * 32) : "memory"); }
+
+// Slice [s0, s0 + n) of cnt candidates for warp w of a team of T.
+__device__ __forceinline__ void team_slice(int cnt, int w, int T, int& s0, int& n) {
+  const int per = (cnt + T - 1) / T;
+  s0 = w * per;
+  n = cnt - s0 < per ? cnt - s0 : per;
+  if (n < 0) n = 0;
+}
+
 // ---------------------------------------------------------------------------
 // Dense back-end: rows of `DT` elements; lanes are split into groups of `lpr`
 // lanes per row, lane `sub` of a group owning 16-byte chunks sub, sub + lpr,
@@ -262,6 +299,34 @@ struct PQBackend {
       scale = ldexpf(1.f, sh);
     }
     __syncwarp();
+  }
+
+  // The same table built by a team of T warps (thread t of the team takes
+  // entries t, t + 32 T, ...); ends with the team at barrier 1.
+  __device__ void init_team(const SearchArgs& a, int qi, int lane, int w, int T, unsigned char* ws, TeamCtl* tc) {
+    WarpSmem s(ws, a.efcap, a.hbits);
+    lut = reinterpret_cast<LutT*>(s.extra);
+    const int m = a.pq_m;
+    const float* q = a.q + (size_t)qi * m * a.pq_dsub;
+    const int t0 = w * 32 + lane, step = T * 32;
+    scale = 1.f;
+    if (!L16) {
+      for (int e = t0; e < m * 256; e += step) lut[e] = entry(a, q, e);
+    } else {
+      float mx = 0.f;
+      for (int e = t0; e < m * 256; e += step) mx = fmaxf(mx, fabsf(entry(a, q, e)));
+      for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(FULL, mx, o));
+      if (lane == 0) tc->wmax[w] = mx;
+      team_bar(T);
+      mx = 0.f;
+      for (int i = 0; i < T; ++i) mx = fmaxf(mx, tc->wmax[i]);
+      int E = 0;
+      if (mx > 0.f) frexpf(mx, &E);  // mx = f * 2^E, f in [0.5, 1)
+      const int sh = E - 15;
+      for (int e = t0; e < m * 256; e += step) lut[e] = __float2half_rn(ldexpf(entry(a, q, e), -sh));
+      scale = ldexpf(1.f, sh);
+    }
+    team_bar(T);
   }
 
   __device__ __forceinline__ void dists(const SearchArgs& a, const int* cid, int cnt, u64* ck, int lane) {
@@ -453,10 +518,39 @@ __device__ __forceinline__ void rerank_dists(const unsigned char* rr, int64_t st
   }
 }
 
+// ---------------------------------------------------------------------------
+// Search teams (the PQ kernel): a CTA of T warps searches one query and shares
+// its lookup table.  Warp 0 runs the search; at every distance evaluation and
+// re-rank batch it posts a command and the candidate count in TeamCtl and the
+// team meets at named barrier 1 twice (go, done), each warp computing the
+// distances of one contiguous slice of the candidates.  Every row is still
+// evaluated by one lane group exactly as in the one-warp search, so the
+// results are the same bit for bit.  Warp 0 reaches every barrier the helpers
+// wait at: the search core has no early exit, and DONE ends the query.
+// ---------------------------------------------------------------------------
+template <int T, class B>
+__device__ __forceinline__ void team_dists(B& be, const SearchArgs& a, const int* cid, int cnt, u64* ck, int lane,
+                                           TeamCtl* tc) {
+  if constexpr (T == 1) {
+    be.dists(a, cid, cnt, ck, lane);
+  } else {
+    if (lane == 0) {
+      tc->cmd = TEAM_DIST;
+      tc->cnt = cnt;
+    }
+    team_bar(T);
+    int s0, n;
+    team_slice(cnt, 0, T, s0, n);
+    be.dists(a, cid + s0, n, ck + s0, lane);
+    team_bar(T);
+  }
+}
+
 // Re-rank the best R entries of W exactly and sort them (cold path, once per
 // query).  Returns the number of re-ranked entries now at the front of W.
 __device__ __noinline__ int rerank_phase(const unsigned char* rr, int rr_dtype, int64_t stride, int nchunks, int lpr,
-                                         int metric, const float* q, int R, u64* W, u64* ck, int* cid, int lane) {
+                                         int metric, const float* q, int R, u64* W, u64* ck, int* cid, int lane,
+                                         TeamCtl* tc, int T) {
   // ask L2 for every re-rank row at once, so that the chunk-by-chunk loads
   // below wait for L2 rather than for DRAM
   for (int j = lane; j < R; j += 32) {
@@ -467,8 +561,18 @@ __device__ __noinline__ int rerank_phase(const unsigned char* rr, int rr_dtype, 
     const int cb = min(64, R - b);
     for (int j = lane; j < cb; j += 32) cid[j] = (int)key_id(W[b + j]);
     __syncwarp();
-    if (rr_dtype == KANN_BF16) rerank_dists<KANN_BF16>(rr, stride, nchunks, lpr, metric, q, cid, cb, ck, lane);
-    else rerank_dists<KANN_F32>(rr, stride, nchunks, lpr, metric, q, cid, cb, ck, lane);
+    int s0 = 0, n = cb;
+    if (T > 1) {
+      if (lane == 0) {
+        tc->cmd = TEAM_RERANK;
+        tc->cnt = cb;
+      }
+      team_bar(T);
+      team_slice(cb, 0, T, s0, n);
+    }
+    if (rr_dtype == KANN_BF16) rerank_dists<KANN_BF16>(rr, stride, nchunks, lpr, metric, q, cid + s0, n, ck + s0, lane);
+    else rerank_dists<KANN_F32>(rr, stride, nchunks, lpr, metric, q, cid + s0, n, ck + s0, lane);
+    if (T > 1) team_bar(T);
     __syncwarp();
     for (int j = lane; j < cb; j += 32) W[b + j] = ck[j];
     __syncwarp();
@@ -521,34 +625,15 @@ __device__ __noinline__ int order_by_sort(u64 e0, u64 e1, bool k0, bool k1, cons
   return cs0 + __popc(s1);
 }
 
-// Shared memory of one warp: W[efcap] keys, candidate keys[64], candidate
-// ids[64], candidate W-ranks[64], then the visited table (1 << hbits words),
-// then back-end scratch.
-struct WarpSmem {
-  u64* W;
-  u64* ck;
-  int* cid;
-  int* clb;
-  uint32_t* H;
-  unsigned char* extra;
-  __device__ __forceinline__ WarpSmem(unsigned char* ws, int efcap, int hbits) {
-    W = reinterpret_cast<u64*>(ws);
-    ck = W + efcap;
-    cid = reinterpret_cast<int*>(ck + 64);
-    clb = cid + 64;
-    H = reinterpret_cast<uint32_t*>(clb + 64);
-    extra = reinterpret_cast<unsigned char*>(H + (1 << hbits));
-  }
-};
-
 template <class B>
 __device__ __forceinline__ uint32_t backend_status(const B&) { return 0u; }
 __device__ __forceinline__ uint32_t backend_status(const SparseBackend& b) {
   return b.trunc ? KANN_QSTAT_QUERY_TRUNCATED : 0u;
 }
 
-template <class B>
-__device__ __forceinline__ void search_one(const SearchArgs& a, B& be, int qi, int lane, unsigned char* ws) {
+template <class B, int T = 1>
+__device__ __forceinline__ void search_one(const SearchArgs& a, B& be, int qi, int lane, unsigned char* ws,
+                                           TeamCtl* tc = nullptr) {
   WarpSmem s(ws, a.efcap, a.hbits);
   u64* W = s.W;
   u64* ck = s.ck;
@@ -567,13 +652,13 @@ __device__ __forceinline__ void search_one(const SearchArgs& a, B& be, int qi, i
   uint32_t st = 0;
   int c_l0d = 0, c_l0e = 0, c_upd = 0, c_uph = 0;
 
-  be.init(a, qi, lane, s.extra);
+  if constexpr (T == 1) be.init(a, qi, lane, s.extra);  // a team builds its table together beforehand
   st |= backend_status(be);
 
   // 1. entry point
   if (lane == 0) cid[0] = a.entry;
   __syncwarp();
-  be.dists(a, cid, 1, ck, lane);
+  team_dists<T>(be, a, cid, 1, ck, lane, tc);
   __syncwarp();
   u64 cur = ck[0];
   c_upd = 1;
@@ -593,7 +678,7 @@ __device__ __forceinline__ void search_one(const SearchArgs& a, B& be, int qi, i
       const int cnt = __popc(bal);
       if (ok) cid[__popc(bal & lt)] = v;
       __syncwarp();
-      be.dists(a, cid, cnt, ck, lane);
+      team_dists<T>(be, a, cid, cnt, ck, lane, tc);
       __syncwarp();
       c_upd += cnt;
       ++c_uph;
@@ -651,7 +736,7 @@ __device__ __forceinline__ void search_one(const SearchArgs& a, B& be, int qi, i
     __syncwarp();
     ++c_l0e;
     if (cnt > 0) {
-      be.dists(a, cid, cnt, ck, lane);
+      team_dists<T>(be, a, cid, cnt, ck, lane, tc);
       __syncwarp();
       c_l0d += cnt;
       // survivors: keys that beat worst(W) and are not in W already
@@ -748,7 +833,7 @@ __device__ __forceinline__ void search_one(const SearchArgs& a, B& be, int qi, i
   if (a.R != 0 && a.rr_data != nullptr) {
     const int R = min(a.R < 0 ? ef : a.R, len);
     nout = rerank_phase(a.rr_data, a.rr_dtype, a.rr_stride, a.rr_nchunks, a.rr_lpr, a.metric, a.q + (size_t)qi * a.d, R, W, ck,
-                        cid, lane);
+                        cid, lane, tc, T);
   }
 
   // 5. output
@@ -810,16 +895,78 @@ __device__ __forceinline__ void run_queries(const SearchArgs& a, B& be) {
   }
 }
 
+// A helper warp of a team: serve warp 0's commands until the query is done.
+template <int T, class B>
+__device__ __forceinline__ void team_helper(const SearchArgs& a, B& be, int qi, int lane, int w, unsigned char* ws,
+                                            TeamCtl* tc) {
+  WarpSmem s(ws, a.efcap, a.hbits);  // warp 0's candidate ids and keys
+  for (;;) {
+    team_bar(T);
+    const int cmd = tc->cmd, cnt = tc->cnt;
+    if (cmd == TEAM_DONE) break;
+    int s0, n;
+    team_slice(cnt, w, T, s0, n);
+    if (cmd == TEAM_DIST) {
+      be.dists(a, s.cid + s0, n, s.ck + s0, lane);
+    } else {
+      const float* q = a.q + (size_t)qi * a.d;
+      if (a.rr_dtype == KANN_BF16)
+        rerank_dists<KANN_BF16>(a.rr_data, a.rr_stride, a.rr_nchunks, a.rr_lpr, a.metric, q, s.cid + s0, n,
+                                s.ck + s0, lane);
+      else
+        rerank_dists<KANN_F32>(a.rr_data, a.rr_stride, a.rr_nchunks, a.rr_lpr, a.metric, q, s.cid + s0, n,
+                               s.ck + s0, lane);
+    }
+    team_bar(T);
+  }
+}
+
+// Queries of a team launch: one query per CTA of T warps at a time (plain:
+// CTA b takes query b; persistent: thread 0 takes the next index from the
+// device counter).  The team builds the query's table, warp 0 searches, the
+// others serve it; TeamCtl sits after the query's shared memory.
+template <int T, class B>
+__device__ __forceinline__ void run_queries_team(const SearchArgs& a, B& be) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  TeamCtl* tc = reinterpret_cast<TeamCtl*>(smem + a.warp_smem);
+  int nq = a.nq;
+  if (a.work_counter && a.d_n) nq = min(nq, max(0, *a.d_n));
+  for (int it = 0;; ++it) {
+    int qi;
+    if (a.work_counter == nullptr) {
+      if (it > 0) break;
+      qi = blockIdx.x;
+    } else {
+      if (threadIdx.x == 0) tc->qi = atomicAdd(a.work_counter, 1);
+      team_bar(T);
+      qi = tc->qi;
+      team_bar(T);
+    }
+    if (qi >= nq) break;
+    be.init_team(a, qi, lane, w, T, smem, tc);
+    if (w == 0) {
+      search_one<B, T>(a, be, qi, lane, smem, tc);
+      if (lane == 0) tc->cmd = TEAM_DONE;
+      team_bar(T);
+    } else {
+      team_helper<T>(a, be, qi, lane, w, smem, tc);
+    }
+  }
+}
+
 template <int DT, int CPLT, bool LEAN, int MET, int LPR>
 __global__ void __launch_bounds__(128, MinBlocks<DT, CPLT, LEAN>::value) search_dense_kernel(const SearchArgs a) {
   DenseBackend<DT, CPLT, LEAN, MET, LPR> be;
   run_queries(a, be);
 }
 
+constexpr int PQ_TEAM = 4;  // warps sharing one query's lookup table
+
 template <int CPLT, bool L16>
-__global__ void __launch_bounds__(128, 1) search_pq_kernel(const SearchArgs a) {
+__global__ void __launch_bounds__(PQ_TEAM * 32, 1) search_pq_kernel(const SearchArgs a) {
   PQBackend<CPLT, L16> be;
-  run_queries(a, be);
+  run_queries_team<PQ_TEAM>(a, be);
 }
 
 template <int DT, int MET>

@@ -961,7 +961,7 @@ __global__ void __launch_bounds__(128, MinBlocks<DT, CPLT, LEAN>::value) search_
   run_queries(a, be);
 }
 
-constexpr int PQ_TEAM = 4;  // warps sharing one query's lookup table
+constexpr int PQ_TEAM = 8;  // warps sharing one query's lookup table (TeamCtl::wmax holds 8)
 
 template <int CPLT, bool L16>
 __global__ void __launch_bounds__(PQ_TEAM * 32, 1) search_pq_kernel(const SearchArgs a) {

@@ -219,29 +219,41 @@ __device__ __forceinline__ float from_ordered(unsigned b) {
 // query's shared bound as last seen.
 struct ScanState {
   float thr;    // own list's k-th score (+inf until the list is full)
-  int slot;     // slot holding it
+  int slot;     // slot holding it (the heap root)
   float thr_g;  // shared bound on the query's k-th score
 };
 
-// Put (dist, col) in the worst slot, find the new worst by (d, id), and when
-// the list is full publish just above its k-th score as the query's bound.
+// A thread's list is a max-heap by (d, id) in its k slots (root = the current
+// k-th, empty slots (+inf, -1)): put (dist, col) in place of the root and sift
+// it down, and when the list is full publish just above its new k-th as the
+// query's bound.
 __device__ __noinline__ ScanState topk_insert(float* ld, int* li, int k, ScanState w, float dist, int col,
                                               unsigned* thr_q) {
-  ld[w.slot] = dist;
-  li[w.slot] = col;
-  float wd = -__int_as_float(0x7f800000);
-  int wid = -2, wi = 0;
-  for (int m = 0; m < k; ++m) {
-    const float d = ld[m];
-    const int id = li[m];
-    if (d > wd || (d == wd && id > wid)) {
-      wd = d;
-      wid = id;
-      wi = m;
+  int i = 0;
+  for (;;) {
+    int c = 2 * i + 1;
+    if (c >= k) break;
+    float cd = ld[c];
+    int cx = li[c];
+    if (c + 1 < k) {
+      const float d2 = ld[c + 1];
+      const int x2 = li[c + 1];
+      if (d2 > cd || (d2 == cd && x2 > cx)) {
+        ++c;
+        cd = d2;
+        cx = x2;
+      }
     }
+    if (!(cd > dist || (cd == dist && cx > col))) break;
+    ld[i] = cd;
+    li[i] = cx;
+    i = c;
   }
+  ld[i] = dist;
+  li[i] = col;
+  const float wd = ld[0];
   w.thr = wd;
-  w.slot = wi;
+  w.slot = 0;
   if (wd != __int_as_float(0x7f800000)) {
     const float up = nextafterf(wd, __int_as_float(0x7f800000));
     if (up < w.thr_g) {

@@ -208,6 +208,22 @@ __device__ __forceinline__ void tc_ld64(uint32_t taddr, float* v) {
   for (int i = 0; i < 64; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// (x0, x1) = (m x0 + c0, m x1 + c1) in one packed FP32 FMA (each lane rounds
+// as fmaf does).
+__device__ __forceinline__ void fma2(float& x0, float& x1, float m, float c0, float c1) {
+  asm("{.reg .b64 A, C, M, R;\n\tmov.b64 A, {%0, %1};\n\tmov.b64 C, {%3, %4};\n\tmov.b64 M, {%2, %2};\n\t"
+      "fma.rn.f32x2 R, A, M, C;\n\tmov.b64 {%0, %1}, R;}"
+      : "+f"(x0), "+f"(x1)
+      : "f"(m), "f"(c0), "f"(c1));
+}
+
+// Three-input minimum (the same value as fminf(fminf(a, b), c)).
+__device__ __forceinline__ float min3(float a, float b, float c) {
+  float r;
+  asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+
 // Inverse of ordered_bits.
 __device__ __forceinline__ float from_ordered(unsigned b) {
   return __uint_as_float((b & 0x80000000u) ? (b & 0x7fffffffu) : ~b);
@@ -433,17 +449,15 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             for (int j = 16 * g; j < 16 * g + 16; j += 4) {
               if (a.metric == KANN_L2) {
                 const float4 n4 = *reinterpret_cast<const float4*>(xw + c0 + j);
-                v[j] = fmaf(-2.f, v[j], n4.x);
-                v[j + 1] = fmaf(-2.f, v[j + 1], n4.y);
-                v[j + 2] = fmaf(-2.f, v[j + 2], n4.z);
-                v[j + 3] = fmaf(-2.f, v[j + 3], n4.w);
+                fma2(v[j], v[j + 1], -2.f, n4.x, n4.y);
+                fma2(v[j + 2], v[j + 3], -2.f, n4.z, n4.w);
               } else {
                 v[j] = -v[j];
                 v[j + 1] = -v[j + 1];
                 v[j + 2] = -v[j + 2];
                 v[j + 3] = -v[j + 3];
               }
-              mn[g] = fminf(mn[g], fminf(fminf(v[j], v[j + 1]), fminf(v[j + 2], v[j + 3])));
+              mn[g] = min3(min3(mn[g], v[j], v[j + 1]), v[j + 2], v[j + 3]);
             }
           }
           // pass 2 (rare: a score beats the current bound), per group of 16

@@ -150,7 +150,9 @@ typedef struct {
                               -1: R = ef_eff.  R must be >= k. */
   int32_t max_hops;        /* cap on layer-0 expansions per query; 0 = 1,000,000 */
   int32_t hash_bits;       /* log2 of the per-query visited table; 0 = automatic */
-  int32_t warps_per_block; /* queries per CTA (one warp each); 0 = automatic */
+  int32_t warps_per_block; /* dense and sparse: queries per CTA (one warp each); 0 = automatic.
+                              A PQ search always runs one query per CTA of 8 warps that
+                              share the query's lookup table */
   int32_t lanes_per_row;   /* lanes sharing one row gather (power of two <= 32); 0 = automatic */
   int32_t lean;            /* dense rows of 2 chunks per lane: 1 = half the row batches in
                               flight for a 64-register budget (more warps per SM), -1 = off,

@@ -223,9 +223,9 @@ int run_pq(const kann_index_t* idx, SearchArgs& a, int wpb, void* stream) {
     a.warp_smem = search_warp_smem_pq(a.efcap, a.hbits, pq.m, a.lut16 != 0);
   }
   if (a.warp_smem + PQ_TEAM_CTL_BYTES > optin) return KANN_ENOMEM;
-  while (wpb > 1 && wpb * a.warp_smem > optin) --wpb;
+  (void)wpb;  // a PQ search runs one query per CTA (a team of warps sharing its table)
   if (a.nq == 0) return KANN_OK;
-  return check_cuda((cudaError_t)launch_search_pq(a, wpb, stream));
+  return check_cuda((cudaError_t)launch_search_pq(a, 1, stream));
 }
 
 int run_sparse(const kann_index_t* idx, SearchArgs& a, const SparseArgs& sa, int wpb, void* stream) {

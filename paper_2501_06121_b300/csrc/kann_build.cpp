@@ -151,12 +151,15 @@ struct Visited {
 };
 
 template <class S, class Q>
-std::vector<DC> search_layer(Builder& B, const S& sp, const Q& q, const std::vector<DC>& eps, int ef, int l,
-                             Visited& vis, std::vector<int32_t>& buf) {
+std::vector<DC> search_layer(Builder& B, const S& sp, const Q& q, int32_t self, const std::vector<DC>& eps, int ef,
+                             int l, Visited& vis, std::vector<int32_t>& buf) {
   vis.next();
+  // the node being inserted is never its own candidate: a concurrent insertion
+  // may already have linked to it on this layer
+  vis.test_set(self);
   std::vector<DC> C, W;  // C: min-heap, W: max-heap
   for (const DC& e : eps) {
-    vis.test_set(e.id);
+    if (vis.test_set(e.id)) continue;
     C.push_back(e);
     std::push_heap(C.begin(), C.end(), DCGreater());
     W.push_back(e);
@@ -212,18 +215,18 @@ template <class S>
 void insert(Builder& B, const S& sp, int32_t i, Visited& vis, std::vector<int32_t>& buf) {
   const int li = B.level[i];
   const auto q = sp.item(i);
-  int32_t ep;
-  int top;
-  {
-    std::lock_guard<std::mutex> g(B.entry_lock);
-    ep = B.entry.load();
-    top = B.top.load();
-    if (ep < 0) {
-      B.entry = i;
-      B.top = li;
-      return;
-    }
+  // A node whose level is above the current top keeps the entry lock for its
+  // whole insertion: a second such node inserted meanwhile would otherwise
+  // link only up to the old top and be left without edges on the new layers.
+  std::unique_lock<std::mutex> glock(B.entry_lock);
+  const int32_t ep = B.entry.load();
+  const int top = B.top.load();
+  if (ep < 0) {
+    B.entry = i;
+    B.top = li;
+    return;
   }
+  if (li <= top) glock.unlock();
   DC cur{sp.dist(q, ep), ep};
   for (int l = top; l > li; --l) {
     bool moved = true;
@@ -241,7 +244,7 @@ void insert(Builder& B, const S& sp, int32_t i, Visited& vis, std::vector<int32_
   }
   std::vector<DC> eps{cur};
   for (int l = std::min(top, li); l >= 0; --l) {
-    std::vector<DC> W = search_layer(B, sp, q, eps, B.efc, l, vis, buf);
+    std::vector<DC> W = search_layer(B, sp, q, i, eps, B.efc, l, vis, buf);
     std::vector<DC> nb = heuristic(sp, W, B.M);
     {
       std::lock_guard<std::mutex> g(B.locks[i]);
@@ -272,12 +275,9 @@ void insert(Builder& B, const S& sp, int32_t i, Visited& vis, std::vector<int32_
     }
     eps = W;
   }
-  if (li > top) {
-    std::lock_guard<std::mutex> g(B.entry_lock);
-    if (li > B.top.load()) {
-      B.top = li;
-      B.entry = i;
-    }
+  if (li > top) {  // still under the entry lock
+    B.top = li;
+    B.entry = i;
   }
 }
 

@@ -209,6 +209,16 @@ int kann_search_batch(const kann_index_t* idx, const float* d_queries, int n, co
  * device's limit). */
 size_t kann_search_workspace_bytes(const kann_index_t* idx, int n, int kmax, int efmax);
 
+/* kann_search_workspace_bytes for a search with options `opts` (nullable =
+ * defaults): the same byte count, and 0 exactly when kann_search_batch with
+ * these n, kmax, efmax and options would be refused (argument checks and the
+ * shared-memory plan are the search's own -- for example a PQ table in FP16
+ * fits where the FP32 table does not, and a PQ search that needs it gives up
+ * visited-table bits to fit).  The pointer options (d_status, d_counters,
+ * d_work_counter, d_n) are ignored. */
+size_t kann_search_workspace_bytes_ex(const kann_index_t* idx, int n, int kmax, int efmax,
+                                      const kann_search_opts* opts);
+
 /* Sparse-query search over a sparse index: queries in CSR (d_q_indptr [n+1]
  * int64, d_q_terms uint16 sorted unique per row, d_q_weights FP32). */
 int kann_search_sparse(const kann_index_t* idx, const int64_t* d_q_indptr, const uint16_t* d_q_terms,
@@ -221,7 +231,10 @@ int kann_search_sparse(const kann_index_t* idx, const int64_t* d_q_indptr, const
  * Scores for L2 are ||x||^2 - 2 q.x (+ ||q||^2) accumulated in FP32; the k best
  * per query are returned sorted by (distance, id) in d_ids / d_dists.
  * d_ws is caller-owned device scratch of at least
- * kann_exact_knn_workspace_bytes(...) bytes.  Errors: KANN_EINVAL. */
+ * kann_exact_knn_workspace_bytes(...) bytes.  d_queries, d_base and d_ws
+ * must be 16-byte aligned, d_ids and d_dists 4-byte aligned, and d a
+ * multiple of 4.  Errors: KANN_EINVAL (sizes, nulls, alignment; nothing is
+ * launched). */
 int kann_exact_knn(const void* d_queries, const void* d_base, int nq, int64_t nb, int d, int metric, int dtype,
                    int k, int32_t* d_ids, float* d_dists, void* d_ws, size_t ws_bytes, void* stream);
 
@@ -249,7 +262,11 @@ int kann_exact_knn_sparse(const int64_t* d_indptr, const uint16_t* d_terms, cons
  * outputs as for kann_exact_knn.
  *   - The first call on a device looks up that array's device address (once
  *     per device, with that device current); make that first call before any
- *     stream capture.
+ *     stream capture.  The address is kept for the life of the process: after
+ *     cudaDeviceReset (or any other teardown of the device's primary context)
+ *     the kept address is stale, so do not call this function again in that
+ *     process.
+ *   - Arguments and their alignment are checked as for kann_exact_knn.
  *   - Returns KANN_EINVAL when the request needs more scratch than the array
  *     holds, i.e. kann_exact_knn_workspace_bytes(nq, nb, d, k, dtype) >
  *     KANN_NOALLOC_SCRATCH_BYTES (split the queries into smaller batches).

@@ -181,6 +181,28 @@ int fill_search_args(const kann_index_t* idx, const float* d_q, int n, int k, in
   return KANN_OK;
 }
 
+// Shared-memory plan of a search with the settings in `a` (efcap, hbits,
+// lut16 filled in): bytes per warp (per team for PQ) and warps per CTA.  A
+// PQ search drops visited-table bits (parity-safe: the table may forget)
+// until its query region fits one CTA.  Both the search and the admission
+// query (kann_search_workspace_bytes) take their answer from here.
+int plan_shared(const kann_index_t* idx, SearchArgs& a, int& wpb) {
+  const int optin = max_optin_smem();
+  if (idx->kind == 1) {
+    const int m = idx->pq.m;
+    a.warp_smem = search_warp_smem_pq(a.efcap, a.hbits, m, a.lut16 != 0);
+    while (a.warp_smem + PQ_TEAM_CTL_BYTES > optin && a.hbits > 8) {
+      --a.hbits;
+      a.warp_smem = search_warp_smem_pq(a.efcap, a.hbits, m, a.lut16 != 0);
+    }
+    wpb = 1;  // one query per CTA (a team of warps sharing its table)
+    return a.warp_smem + PQ_TEAM_CTL_BYTES > optin ? KANN_ENOMEM : KANN_OK;
+  }
+  a.warp_smem = idx->kind == 2 ? search_warp_smem_sparse(a.efcap, a.hbits) : search_warp_smem(a.efcap, a.hbits);
+  while (wpb > 1 && wpb * a.warp_smem > optin) --wpb;
+  return a.warp_smem > optin ? KANN_ENOMEM : KANN_OK;
+}
+
 int run_dense(const kann_index_t* idx, SearchArgs& a, int wpb, void* stream) {
   const kann_vectors_desc& v = idx->v;
   a.data = (const unsigned char*)v.d_data;
@@ -194,11 +216,8 @@ int run_dense(const kann_index_t* idx, SearchArgs& a, int wpb, void* stream) {
   if ((a.nchunks + a.lpr - 1) / a.lpr > 8) return KANN_EINVAL;
   if ((a.nchunks + a.lpr - 1) / a.lpr != 2) a.lean = 0;  // the lean form exists for 2 chunks per lane
   if (a.nq > 0 && (!a.q || !aligned16(a.q))) return KANN_EINVAL;
-  a.warp_smem = search_warp_smem(a.efcap, a.hbits);
-  const int optin = max_optin_smem();
-  while (wpb > 1 && wpb * a.warp_smem > optin) --wpb;
-  if (a.warp_smem > optin) return KANN_ENOMEM;
-  if (a.nq == 0) return KANN_OK;
+  const int rc = plan_shared(idx, a, wpb);
+  if (rc != KANN_OK || a.nq == 0) return rc;
   return check_cuda((cudaError_t)launch_search_dense(a, v.dtype, wpb, stream));
 }
 
@@ -216,27 +235,16 @@ int run_pq(const kann_index_t* idx, SearchArgs& a, int wpb, void* stream) {
   if (a.lpr > a.nchunks) a.lpr = lanes_per_row(a.nchunks);
   if ((a.nchunks + a.lpr - 1) / a.lpr > 4) return KANN_EINVAL;
   if (a.nq > 0 && (!a.q || !aligned16(a.q))) return KANN_EINVAL;
-  const int optin = max_optin_smem();
-  a.warp_smem = search_warp_smem_pq(a.efcap, a.hbits, pq.m, a.lut16 != 0);
-  while (a.warp_smem + PQ_TEAM_CTL_BYTES > optin && a.hbits > 8) {
-    --a.hbits;
-    a.warp_smem = search_warp_smem_pq(a.efcap, a.hbits, pq.m, a.lut16 != 0);
-  }
-  if (a.warp_smem + PQ_TEAM_CTL_BYTES > optin) return KANN_ENOMEM;
-  (void)wpb;  // a PQ search runs one query per CTA (a team of warps sharing its table)
-  if (a.nq == 0) return KANN_OK;
+  const int rc = plan_shared(idx, a, wpb);
+  if (rc != KANN_OK || a.nq == 0) return rc;
   return check_cuda((cudaError_t)launch_search_pq(a, 1, stream));
 }
 
 int run_sparse(const kann_index_t* idx, SearchArgs& a, const SparseArgs& sa, int wpb, void* stream) {
   if (a.R != 0) return KANN_EINVAL;
   a.metric = KANN_IP;
-  a.warp_smem = search_warp_smem_sparse(a.efcap, a.hbits);
-  const int optin = max_optin_smem();
-  while (wpb > 1 && wpb * a.warp_smem > optin) --wpb;
-  if (a.warp_smem > optin) return KANN_ENOMEM;
-  if (a.nq == 0) return KANN_OK;
-  (void)idx;
+  const int rc = plan_shared(idx, a, wpb);
+  if (rc != KANN_OK || a.nq == 0) return rc;
   return check_cuda((cudaError_t)launch_search_sparse(a, sa, wpb, stream));
 }
 
@@ -396,20 +404,43 @@ int kann_search_batch(const kann_index_t* idx, const float* d_queries, int n, co
   return KANN_EINVAL;
 }
 
-size_t kann_search_workspace_bytes(const kann_index_t* idx, int n, int kmax, int efmax) {
+size_t kann_search_workspace_bytes_ex(const kann_index_t* idx, int n, int kmax, int efmax,
+                                      const kann_search_opts* opts) {
   if (!idx || n < 0 || kmax < 1) return 0;
-  const int efmax_eff = efmax > kmax ? efmax : kmax;
-  if (efmax_eff > KANN_MAX_EF) return 0;
-  int efcap = 32;
-  while (efcap < efmax_eff) efcap <<= 1;
-  const int hbits = default_hbits(efmax_eff);
-  int smem = search_warp_smem(efcap, hbits);
-  if (idx->kind == 1) smem = search_warp_smem_pq(efcap, hbits, idx->pq.m) + PQ_TEAM_CTL_BYTES;
-  if (idx->kind == 2) smem = search_warp_smem_sparse(efcap, hbits);
-  if (smem > max_optin_smem()) return 0;
+  // the search's own argument checks and shared-memory plan decide whether it
+  // can run (the batch is sized by n below; no device pointer is needed)
+  SearchArgs a;
+  int wpb = 4;
+  kann_search_opts o;
+  if (opts) {
+    o = *opts;
+    o.d_n = nullptr;  // pointer options do not change what a batch needs
+    o.d_work_counter = nullptr;
+  }
+  if (fill_search_args(idx, nullptr, 0, kmax, efmax, kmax, efmax, nullptr, nullptr, nullptr, nullptr,
+                       opts ? &o : nullptr, a, wpb) != KANN_OK)
+    return 0;
+  if (idx->kind == 2 && a.R != 0) return 0;
+  if (idx->kind == 0) {
+    const int nchunks = idx->v.d * elem_size(idx->v.dtype) / 16;
+    int lpr = a.lpr_override ? a.lpr_override : lanes_per_row(nchunks, default_chunks_per_lane(idx->v.dtype));
+    if (lpr > nchunks && nchunks >= 1) lpr = lanes_per_row(nchunks);
+    if ((nchunks + lpr - 1) / lpr > 8) return 0;
+  }
+  if (idx->kind == 1) {
+    const int nchunks = idx->pq.m / 16;
+    int lpr = a.lpr_override ? a.lpr_override : lanes_per_row(nchunks);
+    if (lpr > nchunks) lpr = lanes_per_row(nchunks);
+    if ((nchunks + lpr - 1) / lpr > 4) return 0;
+  }
+  if (plan_shared(idx, a, wpb) != KANN_OK) return 0;
   const int d = idx->kind == 1 ? idx->pq.m * idx->pq.dsub : idx->v.d;
   const size_t q = idx->kind == 2 ? (size_t)(n + 1) * 8 : (size_t)n * (size_t)d * 4;
   return q + (size_t)n * 8 + (size_t)n * (size_t)kmax * 8 + (size_t)n * 4 + 8;
+}
+
+size_t kann_search_workspace_bytes(const kann_index_t* idx, int n, int kmax, int efmax) {
+  return kann_search_workspace_bytes_ex(idx, n, kmax, efmax, nullptr);
 }
 
 int kann_search_sparse(const kann_index_t* idx, const int64_t* d_q_indptr, const uint16_t* d_q_terms,

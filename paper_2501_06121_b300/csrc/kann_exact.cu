@@ -210,6 +210,11 @@ extern "C" int kann_exact_knn(const void* d_queries, const void* d_base, int nq,
   if (d % 4 != 0) return KANN_EINVAL;
   if (nq == 0) return KANN_OK;
   if (!d_queries || !d_base || !d_ids || !d_dists || !d_ws) return KANN_EINVAL;
+  // row loads are 16-byte vectors (FP32) or TMA boxes (tensor-core path);
+  // the workspace holds 8-byte keys and a 16-byte aligned error word
+  const auto misaligned = [](const void* p, uintptr_t a) { return ((uintptr_t)p & (a - 1)) != 0; };
+  if (misaligned(d_queries, 16) || misaligned(d_base, 16) || misaligned(d_ws, 16)) return KANN_EINVAL;
+  if (misaligned(d_ids, 4) || misaligned(d_dists, 4)) return KANN_EINVAL;
   if (nb == 0 || nb >= ((int64_t)1 << 31)) return KANN_EINVAL;
   if (ws_bytes < kann_exact_knn_workspace_bytes(nq, nb, d, k, dtype)) return KANN_EINVAL;
   if (exact_tc_supported(dtype, d, k)) {

@@ -84,6 +84,7 @@ def _lib():
             "kann_search_batch": (I, [P, P, I, P, P, I, I, P, P, P, P]),
             "kann_search_sparse": (I, [P, P, P, P, I, I, I, P, P, P, P]),
             "kann_search_workspace_bytes": (SZ, [P, I, I, I]),
+            "kann_search_workspace_bytes_ex": (SZ, [P, I, I, I, P]),
             "kann_exact_knn": (I, [P, P, I, I64, I, I, I, I, P, P, P, SZ, P]),
             "kann_exact_knn_workspace_bytes": (SZ, [I, I64, I, I, I]),
             "kann_quantize": (I, [P, I64, I, I, P, P, P]),
@@ -253,11 +254,15 @@ def kann_search_batch(index, queries, k, ef, kmax=None, efmax=None, ids=None, di
     return ids, dists
 
 
-def kann_search_workspace_bytes(index, n, kmax, efmax):
+def kann_search_workspace_bytes(index, n, kmax, efmax, **opts):
     """Device bytes a batch of n queries (k <= kmax, ef <= efmax) needs besides
     the index (queries, k/ef words, outputs, status, counters); 0 if no search
-    with these settings can run."""
-    return int(_lib().kann_search_workspace_bytes(index.handle, n, kmax, efmax))
+    with these settings (and search options `opts`, as for kann_search_ex)
+    can run."""
+    if not opts:
+        return int(_lib().kann_search_workspace_bytes(index.handle, n, kmax, efmax))
+    o = _opts(**opts)
+    return int(_lib().kann_search_workspace_bytes_ex(index.handle, n, kmax, efmax, ctypes.byref(o)))
 
 
 def kann_search_sparse(index, q_indptr, q_terms, q_weights, k, ef, ids=None, dists=None, stream=None, **opts):
@@ -279,22 +284,46 @@ def kann_exact_knn_workspace_bytes(nq, nb, d, k, dtype=KANN_F32):
     return int(_lib().kann_exact_knn_workspace_bytes(nq, nb, d, k, dtype))
 
 
+def _exact_args(fn, queries, base, k, dtype, ids, dists):
+    """Shape and type checks shared by the exact k-NN calls (the library reads
+    nq x d and nb x d elements of `dtype` and writes nq x k outputs, so a
+    mismatch here would be an out-of-bounds access on the device)."""
+    _require_cuda(queries, base, ids, dists)
+    if dtype not in (KANN_F32, KANN_F16, KANN_BF16):
+        raise ValueError("%s: dtype must be KANN_F32, KANN_F16 or KANN_BF16" % fn)
+    want = _TORCH_DTYPE[dtype]
+    if queries.dim() != 2 or base.dim() != 2 or base.shape[1] != queries.shape[1]:
+        raise ValueError("%s: queries [nq, d] and base [nb, d] must share d" % fn)
+    if queries.dtype != want or base.dtype != want:
+        raise ValueError("%s: queries and base must be %s for this dtype, got %s / %s"
+                         % (fn, want, queries.dtype, base.dtype))
+    if queries.device != base.device:
+        raise ValueError("%s: queries and base must be on the same device" % fn)
+    nq = queries.shape[0]
+    for t, tt, name in ((ids, torch.int32, "ids"), (dists, torch.float32, "dists")):
+        if t is not None and (tuple(t.shape) != (nq, k) or t.dtype != tt or t.device != queries.device):
+            raise ValueError("%s: %s must be a [%d, %d] %s tensor on %s" % (fn, name, nq, k, tt, queries.device))
+    if ids is None:
+        ids = torch.empty((nq, k), dtype=torch.int32, device=queries.device)
+    if dists is None:
+        dists = torch.empty((nq, k), dtype=torch.float32, device=queries.device)
+    return ids, dists
+
+
 def kann_exact_knn(queries, base, k, metric, dtype=KANN_F32, ws=None, ids=None, dists=None, stream=None):
     """Brute-force k-NN: queries [nq, d], base [nb, d] device tensors in `dtype`."""
-    _require_cuda(queries, base)
+    ids, dists = _exact_args("kann_exact_knn", queries, base, k, dtype, ids, dists)
     nq, d = queries.shape
     nb = base.shape[0]
     dev = queries.device
-    need = kann_exact_knn_workspace_bytes(nq, nb, d, k, dtype)
-    if ws is None:
-        ws = torch.empty(max(need, 16), dtype=torch.uint8, device=dev)
-    if ids is None:
-        ids = torch.empty((nq, k), dtype=torch.int32, device=dev)
-    if dists is None:
-        dists = torch.empty((nq, k), dtype=torch.float32, device=dev)
-    _check("kann_exact_knn", _lib().kann_exact_knn(_dev(queries), _dev(base), nq, nb, d, metric, dtype, k, _dev(ids),
-                                                   _dev(dists), _dev(ws), ws.numel() * ws.element_size(),
-                                                   _stream(stream)))
+    with torch.cuda.device(dev):
+        need = kann_exact_knn_workspace_bytes(nq, nb, d, k, dtype)
+        if ws is None:
+            ws = torch.empty(max(need, 16), dtype=torch.uint8, device=dev)
+        _require_cuda(ws)
+        _check("kann_exact_knn", _lib().kann_exact_knn(_dev(queries), _dev(base), nq, nb, d, metric, dtype, k,
+                                                       _dev(ids), _dev(dists), _dev(ws),
+                                                       ws.numel() * ws.element_size(), _stream(stream)))
     return ids, dists
 
 
@@ -403,21 +432,20 @@ def kann_exact_knn_noalloc(queries, base, k, metric, dtype=KANN_F32, ids=None, d
     Raises ValueError before calling when the request needs more scratch than
     KANN_NOALLOC_SCRATCH_BYTES; calls that overlap on the GPU must not run
     concurrently (they share the array)."""
-    _require_cuda(queries, base, ids, dists)
     nq, d = queries.shape
     nb = base.shape[0]
     need = kann_exact_knn_workspace_bytes(nq, nb, d, k, dtype)
     if need > KANN_NOALLOC_SCRATCH_BYTES:
         raise ValueError("kann_exact_knn_noalloc: %d queries need %d bytes of scratch, more than the %d-byte "
                          "static array; split the queries" % (nq, need, KANN_NOALLOC_SCRATCH_BYTES))
-    if ids is None:
-        ids = torch.empty((nq, k), dtype=torch.int32, device=queries.device)
-    if dists is None:
-        dists = torch.empty((nq, k), dtype=torch.float32, device=queries.device)
+    ids, dists = _exact_args("kann_exact_knn_noalloc", queries, base, k, dtype, ids, dists)
     f = _lib().kann_exact_knn_noalloc
     P, I = ctypes.c_void_p, ctypes.c_int
     f.restype = I
     f.argtypes = [P, P, I, ctypes.c_int64, I, I, I, I, P, P, P]
-    _check("kann_exact_knn_noalloc", f(_dev(queries), _dev(base), nq, nb, d, metric, dtype, k, _dev(ids),
-                                       _dev(dists), _stream(stream)))
+    # the library looks up the static array of the current device: make it the
+    # device the tensors live on
+    with torch.cuda.device(queries.device):
+        _check("kann_exact_knn_noalloc", f(_dev(queries), _dev(base), nq, nb, d, metric, dtype, k, _dev(ids),
+                                           _dev(dists), _stream(stream)))
     return ids, dists

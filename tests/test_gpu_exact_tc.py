@@ -86,3 +86,35 @@ def test_large_k_falls_back_to_cuda_cores():
     torch.cuda.synchronize()
     oi, od = O.exact_dense(X, Q, 40, O.L2)
     assert np.array_equal(gi.cpu().numpy(), oi)
+
+
+# ------------------------------------------------------------------ argument checks
+def test_exact_knn_rejects_mismatched_arguments_before_launch():
+    # each of these would make the kernel read or write past a buffer's end
+    Q = torch.zeros((10, 64), dtype=torch.float32, device="cuda")
+    X = torch.zeros((500, 64), dtype=torch.float32, device="cuda")
+    with pytest.raises(ValueError):  # half-precision data under the FP32 default
+        K.kann_exact_knn(Q.half(), X.half(), 5, K.KANN_L2)
+    with pytest.raises(ValueError):  # dtype says BF16, tensors are FP16
+        K.kann_exact_knn(Q.half(), X.half(), 5, K.KANN_L2, dtype=K.KANN_BF16)
+    with pytest.raises(ValueError):  # base rows of another width
+        K.kann_exact_knn(Q, X[:, :32].contiguous(), 5, K.KANN_L2)
+    with pytest.raises(ValueError):  # ids too small for [nq, k]
+        K.kann_exact_knn(Q, X, 5, K.KANN_L2, ids=torch.empty((10, 4), dtype=torch.int32, device="cuda"))
+    with pytest.raises(ValueError):  # dists of the wrong type
+        K.kann_exact_knn(Q, X, 5, K.KANN_L2, dists=torch.empty((10, 5), dtype=torch.float16, device="cuda"))
+    with pytest.raises(ValueError):
+        K.kann_exact_knn_noalloc(Q.bfloat16(), X.bfloat16(), 5, K.KANN_L2, dtype=K.KANN_F16)
+
+
+@pytest.mark.parametrize("which", ["queries", "base"])
+def test_exact_knn_rejects_misaligned_rows(which):
+    # a tensor that starts one element into its buffer: the library returns
+    # KANN_EINVAL instead of issuing misaligned 16-byte loads
+    buf = torch.zeros(500 * 64 + 8, dtype=torch.float32, device="cuda")
+    off = buf[1:1 + 500 * 64].view(500, 64)
+    Q = off[:10].contiguous() if which == "base" else off[:10]
+    X = off if which == "base" else torch.zeros((500, 64), dtype=torch.float32, device="cuda")
+    with pytest.raises(K.KannError) as e:
+        K.kann_exact_knn(Q, X, 5, K.KANN_L2)
+    assert e.value.status == K.KANN_EINVAL

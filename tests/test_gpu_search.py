@@ -73,7 +73,7 @@ def test_fp32_l2_parity_cfg1(cfg1_small):
     # the 100-query set at ef = 64, k = 10
     oi, _, _ = O.search_dense(g, X, Q[:100], 10, 64, O.L2)
     gi, _ = search(idx, Q[:100], 10, 64)
-    assert id_set_match_fraction(gi, oi) >= 0.99
+    assert id_set_match_fraction(gi, oi) >= 0.999
 
 
 def test_counters_match_oracle_work(int_small):
@@ -159,7 +159,7 @@ def test_e4m3_parity_across_row_widths(int_dims, d):
     c, s = codes.cpu().numpy(), scale.cpu().numpy()
     oi, od, _ = O.search_dense(g, c, Q, 10, 48, O.L2, dtype=O.DT_E4M3, scale=s)
     gi, gd = search(idx, Q, 10, 48)
-    assert id_set_match_fraction(gi, oi) >= 0.99
+    assert id_set_match_fraction(gi, oi) >= 0.999
     check_dists(c, Q, gi, gd, O.L2, dtype=O.DT_E4M3, scale=s)
 
 

@@ -46,7 +46,8 @@ extern "C" {
 
 /* ---- per-query status bits (optional d_status output of kann_search_ex) -*/
 #define KANN_QSTAT_HOPCAP 1u    /* layer-0 expansions hit opts.max_hops; result is the W reached */
-#define KANN_QSTAT_FORGOT 2u    /* the visited table was cleared at least once (results unaffected) */
+#define KANN_QSTAT_FORGOT 2u    /* the visited table forgot ids (cleared, or an id found no free slot;
+                                   results unaffected, the forgotten ids were evaluated again) */
 #define KANN_QSTAT_BAD_ID 4u    /* an adjacency entry >= n was met and skipped */
 #define KANN_QSTAT_QUERY_TRUNCATED 8u /* sparse query with more than 512 terms: the excess was dropped */
 
@@ -58,6 +59,10 @@ extern "C" {
 #define KANN_F16 1   /* IEEE binary16, round-to-nearest-even from FP32 */
 #define KANN_BF16 2  /* bfloat16, round-to-nearest-even from FP32 */
 #define KANN_E4M3 3  /* OCP FP8 E4M3 with a per-vector FP32 scale s: x = s * code */
+
+#define KANN_VISITED_AUTO 0     /* kann_search_opts.visited_format */
+#define KANN_VISITED_COMPACT 1
+#define KANN_VISITED_WIDE 2
 
 /* Search limits of this build. */
 #define KANN_MAX_EF 1024    /* ef_eff = max(ef, k) must not exceed this */
@@ -149,7 +154,8 @@ typedef struct {
                               candidates from the index's rerank copy (FP32 arithmetic);
                               -1: R = ef_eff.  R must be >= k. */
   int32_t max_hops;        /* cap on layer-0 expansions per query; 0 = 1,000,000 */
-  int32_t hash_bits;       /* log2 of the per-query visited table; 0 = automatic */
+  int32_t hash_bits;       /* log2 of the slots of the per-query visited table (5..16);
+                              0 = automatic (4,096 compact slots; wide: >= 8 efmax, 1,024..8,192) */
   int32_t warps_per_block; /* dense and sparse: queries per CTA (one warp each); 0 = automatic.
                               A PQ search always runs one query per CTA of 8 warps that
                               share the query's lookup table */
@@ -173,6 +179,13 @@ typedef struct {
   const int32_t* d_n;      /* persistent mode only, nullable: device int holding the number
                               of queries to run (clamped to n), read by the kernel -- lets a
                               captured CUDA graph serve batches of varying size */
+  int32_t visited_format;  /* visited table: 0 = automatic (compact when the index allows),
+                              1 = compact: 16-bit slots in buckets of 8, an id stored as an
+                              invertible multiply of its bits split into bucket and slot value
+                              (needs n <= 2^(hash_bits + 12); KANN_EINVAL otherwise),
+                              2 = wide: 32-bit id slots.  Both may forget ids (a forgotten id
+                              is evaluated again), neither reports an unvisited id as visited,
+                              so results do not depend on this choice */
 } kann_search_opts;
 
 /* HNSW K-NN-SEARCH (Malkov & Yashunin Alg. 5) for n dense FP32 queries

@@ -95,10 +95,38 @@ __global__ void validate_graph_kernel(kann_graph_desc g, int* bad) {
   if (local) atomicOr(bad, 1);
 }
 
-int default_hbits(int efmax) {
+// Default visited-table size (log2 of its slots).  Wide (32-bit) table:
+// 2^hbits >= 8 efmax, 10..13.  Compact (16-bit) table: 4,096 slots (8 KB),
+// which holds the ~1,700-4,000 ids a search of 1M items visits at ef 56-512
+// without filling up, and at ef <= 64 keeps six 4-warp CTAs per SM.
+int default_hbits(int efmax, bool compact) {
+  if (compact) return 12;
   int h = 10;
   while ((1 << h) < 8 * efmax && h < 13) ++h;
   return h;
+}
+
+int ceil_log2(int64_t n) {
+  int k = 0;
+  while (((int64_t)1 << k) < n) ++k;
+  return k;
+}
+
+// Visited-table layout for 2^hbits slots over ids < n: compact when every id
+// maps to a bucket of the table and a slot value of at most 16 bits
+// (1 + the low vis_r <= 15 bits of the multiplied id), else wide.
+bool set_visited(SearchArgs& a, int hbits, bool want_compact) {
+  a.hbits = hbits;
+  const int kb = ceil_log2(a.n), bb = hbits - 3;
+  const int k = kb > bb ? kb : bb;
+  if (want_compact && k - bb <= 15) {
+    a.vis_k = k;
+    a.vis_r = k - bb;
+    return true;
+  }
+  a.vis_k = 0;
+  a.vis_r = -1;
+  return false;
 }
 
 int max_optin_smem() {
@@ -138,6 +166,7 @@ int fill_search_args(const kann_index_t* idx, const float* d_q, int n, int k, in
   a.out_d = d_dists;
   a.max_hops = 1000000;
   int hbits = 0;
+  int vformat = 0;
   wpb = 4;
   int R = 0;
   if (opts) {
@@ -156,6 +185,8 @@ int fill_search_args(const kann_index_t* idx, const float* d_q, int n, int k, in
     a.lean = opts->lean > 0 ? 1 : 0;
     if (opts->pq_lut_f16 < 0 || opts->pq_lut_f16 > 1) return KANN_EINVAL;
     a.lut16 = opts->pq_lut_f16;
+    if (opts->visited_format < 0 || opts->visited_format > 2) return KANN_EINVAL;
+    vformat = opts->visited_format;
     R = opts->rerank;
     if (R < -1) return KANN_EINVAL;
     a.work_counter = opts->d_work_counter;
@@ -174,10 +205,11 @@ int fill_search_args(const kann_index_t* idx, const float* d_q, int n, int k, in
     // distances to an FP32 traversal when the copy is FP32)
     a.rr_lpr = lanes_per_row(a.rr_nchunks, default_chunks_per_lane(idx->rr.dtype));
   }
-  a.hbits = hbits ? hbits : default_hbits(a.efmax);
-  int efcap = 32;
-  while (efcap < a.efmax) efcap <<= 1;
-  a.efcap = efcap;
+  // visited table: compact unless asked for wide (or the ids do not fit it)
+  const bool compact_ok = set_visited(a, hbits ? hbits : default_hbits(a.efmax, true), true);
+  if (vformat == 1 && !compact_ok) return KANN_EINVAL;
+  if (vformat == 2 || !compact_ok) set_visited(a, hbits ? hbits : default_hbits(a.efmax, false), false);
+  a.efcap = (a.efmax + 31) / 32 * 32;  // beam capacity: efmax rounded up to whole warp rows
   return KANN_OK;
 }
 
@@ -190,15 +222,17 @@ int plan_shared(const kann_index_t* idx, SearchArgs& a, int& wpb) {
   const int optin = max_optin_smem();
   if (idx->kind == 1) {
     const int m = idx->pq.m;
-    a.warp_smem = search_warp_smem_pq(a.efcap, a.hbits, m, a.lut16 != 0);
+    a.warp_smem = search_warp_smem_pq(a.efcap, a.hbits, a.vis_r >= 0, m, a.lut16 != 0);
     while (a.warp_smem + PQ_TEAM_CTL_BYTES > optin && a.hbits > 8) {
-      --a.hbits;
-      a.warp_smem = search_warp_smem_pq(a.efcap, a.hbits, m, a.lut16 != 0);
+      set_visited(a, a.hbits - 1, a.vis_r >= 0);
+      a.warp_smem = search_warp_smem_pq(a.efcap, a.hbits, a.vis_r >= 0, m, a.lut16 != 0);
     }
     wpb = 1;  // one query per CTA (a team of warps sharing its table)
     return a.warp_smem + PQ_TEAM_CTL_BYTES > optin ? KANN_ENOMEM : KANN_OK;
   }
-  a.warp_smem = idx->kind == 2 ? search_warp_smem_sparse(a.efcap, a.hbits) : search_warp_smem(a.efcap, a.hbits);
+  const bool compact = a.vis_r >= 0;
+  a.warp_smem = idx->kind == 2 ? search_warp_smem_sparse(a.efcap, a.hbits, compact)
+                               : search_warp_smem(a.efcap, a.hbits, compact);
   while (wpb > 1 && wpb * a.warp_smem > optin) --wpb;
   return a.warp_smem > optin ? KANN_ENOMEM : KANN_OK;
 }

@@ -95,6 +95,62 @@ __device__ __forceinline__ void warp_smem_sort(u64* A, int P, int lane) {
   }
 }
 
+// Ascending sort of A[0..n), any n, by one warp.  A bitonic network in the
+// form whose comparators always put the smaller key at the lower index (each
+// merge stage of block size k starts by comparing i with its mirror
+// i ^ (k - 1), then halves as usual).  Positions n .. P - 1 (P the next power
+// of two) act as +inf padding: a comparator never moves the larger key to
+// the lower index, so one that reaches past n would leave both keys in place
+// and is skipped -- nothing beyond A[n) is read or written.
+__device__ __forceinline__ void warp_smem_sort_n(u64* A, int n, int lane) {
+  int P = 1;
+  while (P < n) P <<= 1;
+  for (int k = 2; k <= P; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      const int flip = (j == (k >> 1)) ? (k - 1) : j;
+      for (int i = lane; i < n; i += 32) {
+        const int l = i ^ flip;
+        if (l > i && l < n) {
+          const u64 x = A[i], y = A[l];
+          if (x > y) {
+            A[i] = y;
+            A[l] = x;
+          }
+        }
+      }
+      __syncwarp();
+    }
+  }
+}
+
+// Packed FP32 pair arithmetic (the sm_100 f32x2 forms: each half is rounded
+// exactly as the scalar instruction would round it).  A distance kept as two
+// partial sums, a0 over the even and a1 over the odd elements of a lane's
+// chunks, costs half the accumulation instructions.
+//   acc_sq2:      (a0, a1) += (t0 * t0, t1 * t1)
+//   acc_diff_sq2: t = (q0 - x0, q1 - x1); (a0, a1) += (t0 * t0, t1 * t1)
+//   acc_mul2:     (a0, a1) += (q0 * x0, q1 * x1)
+__device__ __forceinline__ void acc_sq2(float& a0, float& a1, float t0, float t1) {
+  asm("{.reg .b64 A, T;\n\tmov.b64 A, {%0, %1};\n\tmov.b64 T, {%2, %3};\n\t"
+      "fma.rn.f32x2 A, T, T, A;\n\tmov.b64 {%0, %1}, A;}"
+      : "+f"(a0), "+f"(a1)
+      : "f"(t0), "f"(t1));
+}
+
+__device__ __forceinline__ void acc_diff_sq2(float& a0, float& a1, float q0, float q1, float x0, float x1) {
+  asm("{.reg .b64 A, Q, X, T;\n\tmov.b64 A, {%0, %1};\n\tmov.b64 Q, {%2, %3};\n\tmov.b64 X, {%4, %5};\n\t"
+      "sub.rn.f32x2 T, Q, X;\n\tfma.rn.f32x2 A, T, T, A;\n\tmov.b64 {%0, %1}, A;}"
+      : "+f"(a0), "+f"(a1)
+      : "f"(q0), "f"(q1), "f"(x0), "f"(x1));
+}
+
+__device__ __forceinline__ void acc_mul2(float& a0, float& a1, float q0, float q1, float x0, float x1) {
+  asm("{.reg .b64 A, Q, X;\n\tmov.b64 A, {%0, %1};\n\tmov.b64 Q, {%2, %3};\n\tmov.b64 X, {%4, %5};\n\t"
+      "fma.rn.f32x2 A, Q, X, A;\n\tmov.b64 {%0, %1}, A;}"
+      : "+f"(a0), "+f"(a1)
+      : "f"(q0), "f"(q1), "f"(x0), "f"(x1));
+}
+
 // 16-byte read-only global load that does not allocate in L1 (random rows).
 __device__ __forceinline__ uint4 ldg_stream16(const void* p) {
   uint4 r;

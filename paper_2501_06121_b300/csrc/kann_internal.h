@@ -41,12 +41,13 @@ struct SearchArgs {
   uint32_t* status;
   int32_t* counters;
   int hbits, max_hops;
+  int vis_k, vis_r;      // compact visited table: id bits and slot-value bits; vis_r < 0: wide table
   int lpr_override;  // 0 = automatic lanes per row
   int* work_counter;     // persistent mode: next query index (zeroed before launch), or null
   const int32_t* d_n;    // persistent mode: device-side query count (<= nq), or null
   int lean;              // dense: half the rows in flight, 64-register budget
   int lut16;             // PQ: per-query table in FP16 with a power-of-two scale
-  int efcap;       // W capacity (power of two >= efmax, >= 32)
+  int efcap;       // W capacity (efmax rounded up to a multiple of 32)
   int warp_smem;   // bytes of shared memory per warp
 };
 
@@ -77,12 +78,13 @@ SearchKernelFn pick_search_f16(int cplt, bool lean, int metric, int lpr_exact);
 SearchKernelFn pick_search_bf16(int cplt, bool lean, int metric, int lpr_exact);
 SearchKernelFn pick_search_e4m3(int cplt, bool lean, int metric, int lpr_exact);
 
-// Per-warp shared memory needed by a dense search with these settings.
-int search_warp_smem(int efcap, int hbits);
-int search_warp_smem_pq(int efcap, int hbits, int m, bool lut16 = false);
+// Per-warp shared memory needed by a dense search with these settings
+// (compact: a visited table of 16-bit slots, else 32-bit).
+int search_warp_smem(int efcap, int hbits, bool compact);
+int search_warp_smem_pq(int efcap, int hbits, bool compact, int m, bool lut16 = false);
 // Shared memory of a PQ search team's control block (after the query's region).
 constexpr int PQ_TEAM_CTL_BYTES = 64;
-int search_warp_smem_sparse(int efcap, int hbits);
+int search_warp_smem_sparse(int efcap, int hbits, bool compact);
 
 // Launchers (kann_search.cu); return a cudaError_t.
 int launch_search_dense(const SearchArgs& a, int dtype, int wpb, void* stream);

@@ -40,8 +40,8 @@ int pow2_at_least(int x) {
 
 }  // namespace
 
-int search_warp_smem(int efcap, int hbits) {
-  return efcap * 8 + 64 * 8 + 64 * 4 + 64 * 4 + (4 << hbits);
+int search_warp_smem(int efcap, int hbits, bool compact) {
+  return efcap * 8 + 64 * 8 + 64 * 4 + ((compact ? 2 : 4) << hbits);
 }
 
 int launch_search_dense(const SearchArgs& a, int dtype, int wpb, void* stream) {
@@ -67,11 +67,13 @@ int launch_search_dense(const SearchArgs& a, int dtype, int wpb, void* stream) {
   return (int)cudaGetLastError();
 }
 
-int search_warp_smem_pq(int efcap, int hbits, int m, bool lut16) {
-  return search_warp_smem(efcap, hbits) + m * 256 * (lut16 ? 2 : 4);
+int search_warp_smem_pq(int efcap, int hbits, bool compact, int m, bool lut16) {
+  return search_warp_smem(efcap, hbits, compact) + m * 256 * (lut16 ? 2 : 4);
 }
 
-int search_warp_smem_sparse(int efcap, int hbits) { return search_warp_smem(efcap, hbits) + SP_QH * 8; }
+int search_warp_smem_sparse(int efcap, int hbits, bool compact) {
+  return search_warp_smem(efcap, hbits, compact) + SP_QH * 8;
+}
 
 int launch_search_pq(const SearchArgs& a, int wpb, void* stream) {
   if (a.nq == 0) return 0;

@@ -20,10 +20,11 @@
 //   4. optional exact FP32 re-rank of the best R entries of W;
 //   5. the k best keys are written out (id -1 / +inf padding).
 //
-// The visited table is a per-warp open-addressing hash in shared memory.  It
-// may forget (it is cleared and refilled with W's ids when half full, and an
-// id that finds no slot within the probe window is not stored) but it never
-// reports an unvisited id as visited.  Forgetting is harmless because an id
+// The visited table is a per-warp hash in shared memory (a compact table of
+// 16-bit slots when the ids allow it, else 32-bit id slots).  It may forget
+// (it is cleared and refilled with W's ids when it fills up, and an id that
+// finds no free slot is not stored) but it never reports an unvisited id as
+// visited.  Forgetting is harmless because an id
 // already in W is never inserted twice (equal keys are detected in the merge),
 // and an id that left W or was rejected is worse than worst(W), which only
 // improves once W is full; the search therefore returns the same W as with an
@@ -44,9 +45,10 @@ constexpr int HASH_MAX_PROBE = 32;
 __device__ __forceinline__ u64 kmask(u64 k) { return k & ~FLAG; }
 __device__ __forceinline__ uint32_t key_id(u64 k) { return (uint32_t)k & 0x7fffffffu; }
 
-// Visited table.  Returns 0 if id is present, 1 if it was inserted now, 2 if
-// it is absent but the probe window is full (treated as unvisited, not stored).
-__device__ __forceinline__ int visit(uint32_t* H, int hbits, uint32_t id) {
+// Wide visited table: 2^hbits 32-bit slots holding ids, open addressing.
+// Returns 0 if id is present, 1 if it was inserted now, 2 if it is absent but
+// the probe window is full (treated as unvisited, not stored).
+__device__ __forceinline__ int visit32(uint32_t* H, int hbits, uint32_t id) {
   const uint32_t mask = (1u << hbits) - 1u;
   uint32_t h = (id * 2654435761u) >> (32 - hbits);
   volatile uint32_t* vh = H;
@@ -62,6 +64,80 @@ __device__ __forceinline__ int visit(uint32_t* H, int hbits, uint32_t id) {
   }
   return 2;
 }
+
+__device__ __forceinline__ uint4 lds_volatile16(const uint32_t* p) {
+  uint4 r;
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ld.volatile.shared.v4.u32 {%0,%1,%2,%3}, [%4];" : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w) : "r"(a));
+  return r;
+}
+
+// Nonzero exactly when one of the two 16-bit halves of x is zero (the
+// borrow-based zero-lane test: with no zero half nothing borrows and no mask
+// bit survives; the lowest zero half always sets its mask bit).
+__device__ __forceinline__ uint32_t zero_halves(uint32_t x) { return (x - 0x00010001u) & ~x & 0x80008000u; }
+
+// Compact visited table: 2^hbits 16-bit slots in buckets of 8 (one 16-byte
+// row).  An id maps to x = (id * VIS_MUL) mod 2^vk -- a bijection of the
+// vk-bit ids, VIS_MUL being odd -- whose bucket is x >> vr and whose slot
+// value is 1 + (x mod 2^vr); a (bucket, value) pair therefore belongs to one
+// id only, so a match is never a false positive.  Empty slots hold 0.  Same
+// returns as visit32 (2: the bucket is full, the id is not stored).
+constexpr uint32_t VIS_MUL = 0x9E3779B1u;
+__device__ __forceinline__ int visit16(uint32_t* H, int vk, int vr, uint32_t id) {
+  const uint32_t x = (id * VIS_MUL) & (0xffffffffu >> (32 - vk));
+  uint32_t* B = H + ((x >> vr) << 2);
+  const uint32_t tag = (x & ((1u << vr) - 1u)) + 1u;
+  const uint32_t tt = tag * 0x00010001u;
+  // each failed CAS means another lane filled a slot of this bucket: at most
+  // eight of them
+  for (int tries = 0; tries < 9; ++tries) {
+    const uint4 v = lds_volatile16(B);
+    if (zero_halves(v.x ^ tt) | zero_halves(v.y ^ tt) | zero_halves(v.z ^ tt) | zero_halves(v.w ^ tt)) return 0;
+    int i;
+    uint32_t w;
+    if (zero_halves(v.x)) {
+      i = 0;
+      w = v.x;
+    } else if (zero_halves(v.y)) {
+      i = 1;
+      w = v.y;
+    } else if (zero_halves(v.z)) {
+      i = 2;
+      w = v.z;
+    } else if (zero_halves(v.w)) {
+      i = 3;
+      w = v.w;
+    } else {
+      return 2;
+    }
+    const uint32_t nw = (w & 0xffffu) == 0u ? (w | tag) : (w | (tag << 16));
+    if (atomicCAS(B + i, w, nw) == w) return 1;
+  }
+  return 2;
+}
+
+// The visited table of one warp (layout chosen on the host: vr >= 0 compact,
+// vr < 0 wide).
+struct Visited {
+  uint32_t* H;
+  int hbits, vk, vr;
+  __device__ __forceinline__ bool compact() const { return vr >= 0; }
+  __device__ __forceinline__ int insert(uint32_t id) const {
+    return compact() ? visit16(H, vk, vr, id) : visit32(H, hbits, id);
+  }
+  // stored ids above which the table is cleared: 3/4 of the compact slots
+  // (buckets of 8 rarely overflow below that), 1/2 of the wide ones
+  __device__ __forceinline__ int limit() const { return compact() ? (3 << hbits) >> 2 : (1 << hbits) >> 1; }
+  __device__ __forceinline__ void clear(int lane) const {
+    if (compact()) {
+      uint4* q = reinterpret_cast<uint4*>(H);
+      for (int i = lane; i < (1 << hbits) / 8; i += 32) q[i] = make_uint4(0u, 0u, 0u, 0u);
+    } else {
+      for (int i = lane; i < (1 << hbits); i += 32) H[i] = HEMPTY;
+    }
+  }
+};
 
 __device__ __forceinline__ int lower_bound_w(const u64* W, int len, u64 key) {
   int lo = 0, hi = len;
@@ -85,8 +161,9 @@ __device__ __forceinline__ int count_le(const int* A, int n, int x) {
 }
 
 // Shared memory of one warp: W[efcap] keys, candidate keys[64], candidate
-// ids[64], candidate W-ranks[64], then the visited table (1 << hbits words),
-// then back-end scratch.
+// ids[64] (which also hold the survivors' W-ranks once the step's distances
+// are done: the two are never live together), then the visited table
+// (2^hbits slots of 2 bytes, compact, or 4 bytes, wide), then back-end scratch.
 struct WarpSmem {
   u64* W;
   u64* ck;
@@ -94,14 +171,16 @@ struct WarpSmem {
   int* clb;
   uint32_t* H;
   unsigned char* extra;
-  __device__ __forceinline__ WarpSmem(unsigned char* ws, int efcap, int hbits) {
+  __device__ __forceinline__ WarpSmem(unsigned char* ws, int efcap, int hbits, bool compact) {
     W = reinterpret_cast<u64*>(ws);
     ck = W + efcap;
     cid = reinterpret_cast<int*>(ck + 64);
-    clb = cid + 64;
-    H = reinterpret_cast<uint32_t*>(clb + 64);
-    extra = reinterpret_cast<unsigned char*>(H + (1 << hbits));
+    clb = cid;
+    H = reinterpret_cast<uint32_t*>(cid + 64);
+    extra = reinterpret_cast<unsigned char*>(H) + ((compact ? 2 : 4) << hbits);
   }
+  __device__ __forceinline__ WarpSmem(unsigned char* ws, const SearchArgs& a)
+      : WarpSmem(ws, a.efcap, a.hbits, a.vis_r >= 0) {}
 };
 
 enum { TEAM_DIST = 1, TEAM_RERANK = 2, TEAM_DONE = 3 };
@@ -209,7 +288,9 @@ struct DenseBackend {
       for (int u = 0; u < U; ++u) {
         if (base + u * rpi >= cnt) break;  // this and later row groups are empty
         const int r = base + u * rpi + grp;
-        float acc = 0.f;
+        // two partial sums per lane: a0 over the even, a1 over the odd
+        // elements of its chunks (in chunk order), then a0 + a1
+        float a0 = 0.f, a1 = 0.f;
 #pragma unroll
         for (int c = 0; c < CPL; ++c) {
           if constexpr (WIDE_SUB) {
@@ -218,24 +299,27 @@ struct DenseBackend {
             for (int i = 0; i < 4; ++i) {
               float t0, t1;
               sub2_wide<DT>(w[i], qr[c][2 * i], qr[c][2 * i + 1], t0, t1);
-              acc = fmaf(t0, t0, acc);
-              acc = fmaf(t1, t1, acc);
+              acc_sq2(a0, a1, t0, t1);
             }
           } else {
             float x[EPC];
             Fmt<DT>::unpack(buf[u][c], x);
 #pragma unroll
-            for (int e = 0; e < EPC; ++e) {
+            for (int e = 0; e < EPC; e += 2) {
               if (MET == KANN_L2) {
-                // E4M3: q - s x in one rounding
-                const float t = (DT == KANN_E4M3) ? fmaf(-x[e], sc[u], qr[c][e]) : qr[c][e] - x[e];
-                acc = fmaf(t, t, acc);
+                if (DT == KANN_E4M3) {
+                  // q - s x in one rounding
+                  acc_sq2(a0, a1, fmaf(-x[e], sc[u], qr[c][e]), fmaf(-x[e + 1], sc[u], qr[c][e + 1]));
+                } else {
+                  acc_diff_sq2(a0, a1, qr[c][e], qr[c][e + 1], x[e], x[e + 1]);
+                }
               } else {
-                acc = fmaf(qr[c][e], x[e], acc);  // E4M3: the row's scale is applied once below
+                acc_mul2(a0, a1, qr[c][e], qr[c][e + 1], x[e], x[e + 1]);  // E4M3: scale applied once below
               }
             }
           }
         }
+        float acc = a0 + a1;
         if (DT == KANN_E4M3 && MET != KANN_L2) acc *= sc[u];
         for (int o = lpr >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
         if (sub == 0 && r < cnt) ck[r] = make_key(MET == KANN_L2 ? acc : -acc, (uint32_t)cid[r]);
@@ -304,7 +388,7 @@ struct PQBackend {
   // The same table built by a team of T warps (thread t of the team takes
   // entries t, t + 32 T, ...); ends with the team at barrier 1.
   __device__ void init_team(const SearchArgs& a, int qi, int lane, int w, int T, unsigned char* ws, TeamCtl* tc) {
-    WarpSmem s(ws, a.efcap, a.hbits);
+    WarpSmem s(ws, a);
     lut = reinterpret_cast<LutT*>(s.extra);
     const int m = a.pq_m;
     const float* q = a.q + (size_t)qi * m * a.pq_dsub;
@@ -457,8 +541,9 @@ struct SparseBackend {
 
 // Exact FP32 distances for the re-rank, from the index's FP32 copy.  Same
 // lane/chunk mapping and summation order as the FP32 dense back-end (chunks
-// in order, elements in order, then the butterfly), so a re-ranked distance
-// is bit-identical to the FP32 traversal distance of the same row.
+// in order, even and odd elements in two partial sums, their sum, then the
+// butterfly), so a re-ranked distance is bit-identical to the FP32 traversal
+// distance of the same row.
 template <int RDT>
 __device__ __forceinline__ void rerank_dists(const unsigned char* rr, int64_t stride, int nchunks, int lpr, int metric,
                                              const float* q, const int* cid, int cnt, u64* ck, int lane) {
@@ -468,13 +553,14 @@ __device__ __forceinline__ void rerank_dists(const unsigned char* rr, int64_t st
   const int sub = lane & (lpr - 1), grp = lane / lpr;
   const int cpl = (nchunks + lpr - 1) / lpr;
   for (int base = 0; base < cnt; base += rpi * U) {
-    float acc[U];
+    float acc[U], acc1[U];  // even / odd element partial sums, as in the traversal
     int ids[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
       const int r = base + u * rpi + grp;
       ids[u] = r < cnt ? cid[r] : -1;
       acc[u] = 0.f;
+      acc1[u] = 0.f;
     }
     for (int c = 0; c < cpl; ++c) {
       const int ch = sub + c * lpr;
@@ -498,19 +584,15 @@ __device__ __forceinline__ void rerank_dists(const unsigned char* rr, int64_t st
         float x[EPC];
         Fmt<RDT>::unpack(buf[u], x);
 #pragma unroll
-        for (int e = 0; e < EPC; ++e) {
-          if (metric == KANN_L2) {
-            const float t = qq[e] - x[e];
-            acc[u] = fmaf(t, t, acc[u]);
-          } else {
-            acc[u] = fmaf(qq[e], x[e], acc[u]);
-          }
+        for (int e = 0; e < EPC; e += 2) {
+          if (metric == KANN_L2) acc_diff_sq2(acc[u], acc1[u], qq[e], qq[e + 1], x[e], x[e + 1]);
+          else acc_mul2(acc[u], acc1[u], qq[e], qq[e + 1], x[e], x[e + 1]);
         }
       }
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      float v = acc[u];
+      float v = acc[u] + acc1[u];
       for (int o = lpr >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
       const int r = base + u * rpi + grp;
       if (sub == 0 && r < cnt) ck[r] = make_key(metric == KANN_L2 ? v : -v, (uint32_t)ids[u]);
@@ -577,20 +659,19 @@ __device__ __noinline__ int rerank_phase(const unsigned char* rr, int rr_dtype, 
     for (int j = lane; j < cb; j += 32) W[b + j] = ck[j];
     __syncwarp();
   }
-  int P = 2;
-  while (P < R) P <<= 1;
-  for (int i = R + lane; i < P; i += 32) W[i] = KEY_MAX;
-  __syncwarp();
-  warp_smem_sort(W, P, lane);
+  warp_smem_sort_n(W, R, lane);
   return R;
 }
 
-// Clear the visited table and put W's ids back (cold path).
-__device__ __noinline__ void reset_visited(uint32_t* H, int hbits, const u64* W, int len, int lane) {
-  for (int i = lane; i < (1 << hbits); i += 32) H[i] = HEMPTY;
+// Clear the visited table and put W's ids back (cold path); returns the
+// number of ids stored.
+__device__ __noinline__ int reset_visited(const Visited& V, const u64* W, int len, int lane) {
+  V.clear(lane);
   __syncwarp();
-  for (int i = lane; i < len; i += 32) visit(H, hbits, key_id(W[i]));
+  int n = 0;
+  for (int i = lane; i < len; i += 32) n += V.insert(key_id(W[i])) == 1;
   __syncwarp();
+  return __reduce_add_sync(FULL, n);
 }
 
 // Survivors of a step (keys that beat worst(W) and are not in W) ordered by a
@@ -634,13 +715,12 @@ __device__ __forceinline__ uint32_t backend_status(const SparseBackend& b) {
 template <class B, int T = 1>
 __device__ __forceinline__ void search_one(const SearchArgs& a, B& be, int qi, int lane, unsigned char* ws,
                                            TeamCtl* tc = nullptr) {
-  WarpSmem s(ws, a.efcap, a.hbits);
+  WarpSmem s(ws, a);
   u64* W = s.W;
   u64* ck = s.ck;
   int* cid = s.cid;
   int* clb = s.clb;
-  uint32_t* H = s.H;
-  const int Hn = 1 << a.hbits;
+  const Visited V{s.H, a.hbits, a.vis_k, a.vis_r};
   const unsigned lt = (1u << lane) - 1u;
 
   int k = a.k, ef = a.ef;
@@ -690,10 +770,10 @@ __device__ __forceinline__ void search_one(const SearchArgs& a, B& be, int qi, i
   }
 
   // 3. layer-0 beam
-  for (int i = lane; i < Hn; i += 32) H[i] = HEMPTY;
+  V.clear(lane);
   __syncwarp();
   if (lane == 0) {
-    visit(H, a.hbits, key_id(cur));
+    V.insert(key_id(cur));
     W[0] = cur;
   }
   __syncwarp();
@@ -726,8 +806,9 @@ __device__ __forceinline__ void search_one(const SearchArgs& a, B& be, int qi, i
     if (v0 >= a.n || v1 >= a.n) st |= KANN_QSTAT_BAD_ID;
     if (v0 >= a.n) v0 = -1;
     if (v1 >= a.n) v1 = -1;
-    const int r0 = v0 >= 0 ? visit(H, a.hbits, (uint32_t)v0) : 0;
-    const int r1 = v1 >= 0 ? visit(H, a.hbits, (uint32_t)v1) : 0;
+    const int r0 = v0 >= 0 ? V.insert((uint32_t)v0) : 0;
+    const int r1 = v1 >= 0 ? V.insert((uint32_t)v1) : 0;
+    if (r0 == 2 || r1 == 2) st |= KANN_QSTAT_FORGOT;
     stored += __popc(__ballot_sync(FULL, r0 == 1)) + __popc(__ballot_sync(FULL, r1 == 1));
     const unsigned b0 = __ballot_sync(FULL, r0 != 0), b1 = __ballot_sync(FULL, r1 != 0);
     const int c0 = __popc(b0), cnt = c0 + __popc(b1);
@@ -820,11 +901,10 @@ __device__ __forceinline__ void search_one(const SearchArgs& a, B& be, int qi, i
         if (lo < cursor) cursor = lo;
       }
     }
-    // visited-table upkeep: keep the load factor at or below one half
-    if (stored > (Hn >> 1)) {
+    // visited-table upkeep: keep the load factor below the table's limit
+    if (stored > V.limit()) {
       st |= KANN_QSTAT_FORGOT;
-      reset_visited(H, a.hbits, W, len, lane);
-      stored = len;
+      stored = reset_visited(V, W, len, lane);
     }
   }
 
@@ -899,7 +979,7 @@ __device__ __forceinline__ void run_queries(const SearchArgs& a, B& be) {
 template <int T, class B>
 __device__ __forceinline__ void team_helper(const SearchArgs& a, B& be, int qi, int lane, int w, unsigned char* ws,
                                             TeamCtl* tc) {
-  WarpSmem s(ws, a.efcap, a.hbits);  // warp 0's candidate ids and keys
+  WarpSmem s(ws, a);  // warp 0's candidate ids and keys
   for (;;) {
     team_bar(T);
     const int cmd = tc->cmd, cnt = tc->cnt;

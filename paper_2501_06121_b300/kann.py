@@ -62,7 +62,8 @@ class kann_search_opts(ctypes.Structure):
                 ("warps_per_block", ctypes.c_int32), ("lanes_per_row", ctypes.c_int32), ("lean", ctypes.c_int32),
                 ("pq_lut_f16", ctypes.c_int32),
                 ("d_status", ctypes.c_void_p), ("d_counters", ctypes.c_void_p),
-                ("d_work_counter", ctypes.c_void_p), ("d_n", ctypes.c_void_p)]
+                ("d_work_counter", ctypes.c_void_p), ("d_n", ctypes.c_void_p),
+                ("visited_format", ctypes.c_int32)]
 
 
 _L = None
@@ -206,13 +207,16 @@ def kann_index_upload(graph, vectors=None, dtype=KANN_F32, metric=KANN_L2, scale
                  M0=int(graph["M0"]))
 
 
+KANN_VISITED_AUTO, KANN_VISITED_COMPACT, KANN_VISITED_WIDE = 0, 1, 2
+
+
 def _opts(rerank=0, max_hops=0, hash_bits=0, warps_per_block=0, lanes_per_row=0, status=None, counters=None,
-          work_counter=None, n_device=None, lean=0, pq_lut_f16=0):
+          work_counter=None, n_device=None, lean=0, pq_lut_f16=0, visited_format=0):
     _require_cuda(status, counters, work_counter, n_device)
     p = lambda t: t.data_ptr() if t is not None else None
     return kann_search_opts(int(rerank), int(max_hops), int(hash_bits), int(warps_per_block), int(lanes_per_row),
                             int(lean), int(pq_lut_f16),
-                            p(status), p(counters), p(work_counter), p(n_device))
+                            p(status), p(counters), p(work_counter), p(n_device), int(visited_format))
 
 
 def kann_search(index, queries, k, ef, ids=None, dists=None, stream=None):

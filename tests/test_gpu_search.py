@@ -163,15 +163,56 @@ def test_e4m3_parity_across_row_widths(int_dims, d):
     check_dists(c, Q, gi, gd, O.L2, dtype=O.DT_E4M3, scale=s)
 
 
-def test_forgetful_table_changes_nothing(int_small):
+@pytest.mark.parametrize("fmt", [K.KANN_VISITED_COMPACT, K.KANN_VISITED_WIDE])
+def test_forgetful_table_changes_nothing(int_small, fmt):
+    # a table of 32 slots forgets almost everything (full buckets or probe
+    # windows, and a clear after nearly every expansion): the results stay
+    # those of a table that never forgets
     X, Q, g = int_small
     idx, _, _ = upload(g.arrays(), X)
-    base_i, base_d = search(idx, Q, 10, 128, hash_bits=14)
+    base_i, base_d = search(idx, Q, 10, 128, hash_bits=14, visited_format=fmt)
     st = torch.zeros(len(Q), dtype=torch.int32, device="cuda")
     cnt = torch.zeros((len(Q), 4), dtype=torch.int32, device="cuda")
-    gi, gd = search(idx, Q, 10, 128, hash_bits=5, status=st, counters=cnt)
+    gi, gd = search(idx, Q, 10, 128, hash_bits=5, status=st, counters=cnt, visited_format=fmt)
     assert np.array_equal(gi, base_i) and np.array_equal(gd, base_d)
     assert np.all((st.cpu().numpy() & K.KANN_QSTAT_FORGOT) != 0)
+
+
+@pytest.mark.parametrize("ef", [16, 64, 300])
+def test_visited_formats_and_sizes_agree_bit_for_bit(int_small, ef):
+    # compact (16-bit slots, ids split into bucket and slot value) and wide
+    # (32-bit id slots) tables of several sizes: the same results, and with a
+    # table that never forgets, the oracle's work counts
+    X, Q, g = int_small
+    idx, _, _ = upload(g.arrays(), X, dtype=K.KANN_F16)
+    oi, od, oc = O.search_dense(g, X, Q, 10, ef, O.L2)
+    for fmt, hb in ((K.KANN_VISITED_COMPACT, 0), (K.KANN_VISITED_COMPACT, 9), (K.KANN_VISITED_COMPACT, 16),
+                    (K.KANN_VISITED_WIDE, 0), (K.KANN_VISITED_WIDE, 15)):
+        cnt = torch.zeros((len(Q), 4), dtype=torch.int32, device="cuda")
+        gi, gd = search(idx, Q, 10, ef, hash_bits=hb, visited_format=fmt, counters=cnt)
+        assert np.array_equal(gi, oi), (fmt, hb)
+        assert np.array_equal(gd.astype(np.float64), od), (fmt, hb)
+        if hb >= 15:
+            assert np.array_equal(cnt.cpu().numpy().astype(np.int64), oc), (fmt, hb)
+
+
+def test_compact_table_needs_room_for_the_ids(int_small):
+    # 2^5 compact slots hold ids of at most 5 + 12 bits: a 20,000-node index
+    # fits, and an explicit request that cannot fit is refused
+    X, Q, g = int_small
+    idx, _, _ = upload(g.arrays(), X)
+    search(idx, Q[:4], 10, 32, hash_bits=5, visited_format=K.KANN_VISITED_COMPACT)
+    big = dict(g.arrays())
+    n = 1 << 18
+    Xb = np.zeros((n, 128), np.float32)
+    garr = dict(n=n, M=big["M"], M0=big["M0"], max_level=0, entry=0, level=np.zeros(n, np.int8),
+                l0=np.full((n, big["M0"]), -1, np.int32), upper_slot=np.full(n, -1, np.int32),
+                upper=np.full((1, 1, big["M"]), -1, np.int32))
+    ib = K.kann_index_upload(K.graph_to_device(garr), vectors=dev(Xb))
+    with pytest.raises(K.KannError):
+        search(ib, Q[:4], 10, 32, hash_bits=5, visited_format=K.KANN_VISITED_COMPACT)
+    gi, _ = search(ib, Q[:4], 10, 32, hash_bits=5)  # automatic: falls back to the wide table
+    assert np.all(gi[:, 0] == 0) and np.all(gi[:, 1:] == -1)
 
 
 # ------------------------------------------------------------------ other measures / formats

@@ -148,10 +148,10 @@ class OracleRunner:
     arithmetic, then an FP64 re-rank on the FP32 vectors (the same path the
     GPU step runs), over a sample of the queries on all host cores."""
 
-    def __init__(self, g, X, ef, threads=0):
+    def __init__(self, g, X, ef, threads=0, og=None):
         import oracle as O
         self.O = O
-        self.og = O.import_graph(g)
+        self.og = og if og is not None else O.import_graph(g)
         self.Xh = O.encode_f16(X)
         self.X = X
         self.ef = ef
@@ -175,11 +175,49 @@ class OracleRunner:
                           "FP64 re-rank), %.1f s on %d threads" % (n, total, self.ef, dt, self.threads)}
 
 
-def cpu_oracle_qps(g, X, Q, ef, seconds=15.0):
+def cpu_model():
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def cpu_oracle_qps(g, X, Q, ef, seconds=12.0, sweep=(), point_seconds=0.8):
+    """The FP64 oracle on the host: all cores at the selected ef (the line's
+    value), one thread at the same ef (the paper's single-threaded query
+    protocol, Sec. 3), and both over the ef sweep on bounded samples."""
     r = OracleRunner(g, X, ef)
     n = int(min(len(Q), max(8 * r.threads, seconds / max(r.per_query_s(Q), 1e-6))))
     dt = r.run(Q[:n])
-    return r.describe(n, len(Q), dt)
+    out = r.describe(n, len(Q), dt)
+    out["cpu_model"] = cpu_model()
+    r1 = OracleRunner(g, X, ef, threads=1, og=r.og)
+    n1 = int(min(len(Q), max(4, 0.5 * seconds / max(r1.per_query_s(Q), 1e-6))))
+    out["one_thread"] = {"value": n1 / r1.run(Q[:n1]), "unit": "queries/s", "cores": 1, "queries": n1}
+    pts = []
+    for e in sweep:
+        p = {"ef": e}
+        for name, runner in (("all_cores", r), ("one_thread", r1)):
+            runner.ef = e
+            per = runner.per_query_s(Q)
+            m = int(min(len(Q), max(runner.threads, point_seconds / max(per, 1e-6))))
+            p[name] = m / runner.run(Q[:m])
+        pts.append(p)
+    r.ef = r1.ef = ef
+    out["by_ef"] = pts
+    return out
+
+
+def launch_kwargs(opts, work_ctr):
+    """kann_search_ex keyword arguments for an autotuned option dict (the
+    persistent form takes the preallocated work counter)."""
+    o = dict(opts)
+    if o.pop("persistent", False):
+        o["work_counter"] = work_ctr
+    return o
 
 
 def select_ef(recalls, key, fixed=None):
@@ -268,6 +306,7 @@ def run_reference(args):
     v = total_q / total_t
     base = runner.describe(total_q, len(Q), total_t)
     base["sample"] += "; %d queries per step" % n_step
+    base["cpu_model"] = cpu_model()
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "queries/s", "n_gpus": 1, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * total_t / max(1, args.steps), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -478,6 +517,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-curve", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="default launch settings instead of the autotuner's")
     ap.add_argument("--serving-seconds", type=float, default=2.0)
     ap.add_argument("--serving-rates", default="5000,20000,50000,100000,200000")
     ap.add_argument("--workload", default="sift1m", choices=["sift1m", "pq768", "sparse100k"])
@@ -559,16 +599,26 @@ def main():
     ids_buf = torch.empty((N_QUERY, K), dtype=torch.int32, device=dev)
     d_buf = torch.empty((N_QUERY, K), dtype=torch.float32, device=dev)
 
-    def timed(index, rr, steps, warm):
+    # launch settings per arm from the autotuner (every candidate must return
+    # the default launch's ids and distances bit for bit)
+    from paper_2501_06121_b300 import autotune as A_
+    work_ctr = torch.zeros(1, dtype=torch.int32, device=dev)
+    t_tune = time.time()
+    tuned16 = A_.tune(idx16, Qd, K, ef, rerank=-1, reps=3) if not args.no_tune else {}
+    tuned32 = A_.tune(idx32, Qd, K, ef, rerank=0, reps=3) if not args.no_tune else {}
+    tune_s = time.time() - t_tune
+    kw16, kw32 = launch_kwargs(tuned16, work_ctr), launch_kwargs(tuned32, work_ctr)
+
+    def timed(index, rr, steps, warm, kw):
         for _ in range(warm):
-            K_.kann_search_ex(index, Qd, K, ef, ids=ids_buf, dists=d_buf, rerank=rr)
+            K_.kann_search_ex(index, Qd, K, ef, ids=ids_buf, dists=d_buf, rerank=rr, **kw)
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
         evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
         evs[0].record(stream)
         for i in range(steps):
-            K_.kann_search_ex(index, Qd, K, ef, ids=ids_buf, dists=d_buf, rerank=rr)
+            K_.kann_search_ex(index, Qd, K, ef, ids=ids_buf, dists=d_buf, rerank=rr, **kw)
             evs[i + 1].record(stream)
         torch.cuda.synchronize()
         per = [evs[i].elapsed_time(evs[i + 1]) for i in range(steps)]
@@ -577,10 +627,10 @@ def main():
     clocks = Clocks(local)
     time.sleep(0.3)
     w0 = time.time()
-    total_ms, per = timed(idx16, -1, args.steps, args.warmup)
+    total_ms, per = timed(idx16, -1, args.steps, args.warmup, kw16)
     clk = clocks.stop(w0 + 1e-3 * 0, time.time())
     total_ms = max_over_ranks(total_ms, world, dev)
-    fp32_ms, _ = timed(idx32, 0, max(3, args.steps // 2), 2)
+    fp32_ms, _ = timed(idx32, 0, max(3, args.steps // 2), 2, kw32)
     fp32_ms /= max(3, args.steps // 2)
 
     qps = job_qps(world, N_QUERY, args.steps, total_ms)
@@ -604,7 +654,7 @@ def main():
 
     def e2e_step():
         Qdev.copy_(Qpin, non_blocking=True)
-        K_.kann_search_ex(idx16, Qdev, K, ef, ids=ids_buf, dists=d_buf, rerank=-1)
+        K_.kann_search_ex(idx16, Qdev, K, ef, ids=ids_buf, dists=d_buf, rerank=-1, **kw16)
         ids_h.copy_(ids_buf, non_blocking=True)
         d_h.copy_(d_buf, non_blocking=True)
 
@@ -644,18 +694,21 @@ def main():
             for name, index, rr, rb in (("fp16_rerank", idx16, -1, bq),
                                         ("fp32", idx32, 0, bq + m[0] * (row32 - row16) + m[2] * (row32 - row16)
                                          - efc * row32)):
+                opt_c = A_.tune(index, Qd, K, efc, rerank=rr, reps=2) if not args.no_tune else {}
+                kwc = launch_kwargs(opt_c, work_ctr)
                 for _ in range(2):
-                    K_.kann_search_ex(index, Qd, K, efc, rerank=rr)
+                    K_.kann_search_ex(index, Qd, K, efc, rerank=rr, **kwc)
                 torch.cuda.synchronize()
                 e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
                 e0.record()
                 for _ in range(5):
-                    cid_, _ = K_.kann_search_ex(index, Qd, K, efc, rerank=rr)
+                    cid_, _ = K_.kann_search_ex(index, Qd, K, efc, rerank=rr, **kwc)
                 e1.record()
                 torch.cuda.synchronize()
                 msc = e0.elapsed_time(e1) / 5
                 point[name] = {"recall@10": recall_at(cid_.cpu().numpy(), gt), "qps": N_QUERY / (msc / 1e3),
-                               "ms": msc, "roofline_frac": N_QUERY * rb / (msc / 1e3) / 1e9 / hbm}
+                               "ms": msc, "roofline_frac": N_QUERY * rb / (msc / 1e3) / 1e9 / hbm,
+                               "launch": opt_c}
             curve.append(point)
 
     serving = None
@@ -664,7 +717,7 @@ def main():
 
     cpu_base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu_base = cpu_oracle_qps(g, X, Q, ef)
+        cpu_base = cpu_oracle_qps(g, X, Q, ef, sweep=EF_SWEEP if not args.no_curve else ())
 
     if rank == 0:
         per_sorted = sorted(per)
@@ -684,6 +737,11 @@ def main():
                                             "p99": per_sorted[min(len(per) - 1, int(0.99 * len(per)))]},
                        "work_per_query": {"l0_dist": c[0], "l0_expansions": c[1], "upper_dist": c[2],
                                           "upper_hops": c[3]},
+                       "launch_settings": {"fp16_rerank": tuned16, "fp32": tuned32, "tune_s": tune_s,
+                                           "rule": "autotuner: fastest of the result-preserving settings "
+                                                   "(visited table layout and size, lanes per row, warps "
+                                                   "per CTA, lean, persistent), same ids and distances "
+                                                   "as the default launch"},
                        "host_cores": os.cpu_count()},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                          "traffic": traffic, "algorithmic_bytes_per_query": bytes_per_q,

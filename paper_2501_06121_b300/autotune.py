@@ -1,12 +1,16 @@
 """Per-index autotuner for the search launch settings.
 
-The settings that do not change results — lanes per row gather, visited
-table size, warps per CTA, plain vs persistent work-stealing launch — are
-timed on a sample of the caller's queries with CUDA events; a setting is
+The settings that do not change results -- lanes per row gather, the
+visited table's layout (compact 16-bit or wide 32-bit slots) and size,
+warps per CTA, the lean register budget, plain vs persistent work-stealing
+launch -- are timed on the caller's queries with CUDA events; a setting is
 accepted only if it returns exactly the same ids and distances as the
 default launch (they all must: the search is defined by (k, ef) alone).
-The winner is cached in a JSON file keyed by the index signature, the GPU
-name and the driver version.
+The table size trades shared memory (hence queries resident per SM) against
+forgotten ids that are evaluated again, and the best point moves with ef
+and with the kernel's register budget, which is why it is measured rather
+than fixed.  The winner is cached in a JSON file keyed by the index
+signature, the GPU name and the driver version.
 """
 import json
 import os
@@ -39,7 +43,8 @@ def _time(index, Q, k, ef, reps, opts):
 
 def tune(index, queries, k, ef, rerank=0, reps=5, cache_path=None, verbose=False):
     """Returns the fastest result-preserving option dict for kann_search_ex
-    (keys lanes_per_row, hash_bits, warps_per_block, lean, persistent)."""
+    (keys lanes_per_row, hash_bits, visited_format, warps_per_block, lean,
+    persistent)."""
     key = _signature(index, k, ef, rerank)
     cache = {}
     if cache_path and os.path.exists(cache_path):
@@ -48,7 +53,8 @@ def tune(index, queries, k, ef, rerank=0, reps=5, cache_path=None, verbose=False
         if key in cache:
             return dict(cache[key]["opts"])
     base_t, (ref_i, ref_d) = _time(index, queries, k, ef, reps, dict(rerank=rerank))
-    best, best_t = dict(lanes_per_row=0, hash_bits=0, warps_per_block=0, lean=0, persistent=False), base_t
+    best = dict(lanes_per_row=0, hash_bits=0, visited_format=0, warps_per_block=0, lean=0, persistent=False)
+    best_t = base_t
     results = []
 
     def trial(o):
@@ -62,13 +68,18 @@ def tune(index, queries, k, ef, rerank=0, reps=5, cache_path=None, verbose=False
         if same and t < best_t:
             best, best_t = dict(o), t
 
-    for lpr in (0, 2, 4, 8, 16, 32):
-        for hb in (0, 9, 10, 11, 12):
-            trial(dict(lanes_per_row=lpr, hash_bits=hb, warps_per_block=0, lean=0, persistent=False))
+    tables = [(K.KANN_VISITED_COMPACT, hb) for hb in (11, 12, 13)] + [(K.KANN_VISITED_WIDE, hb) for hb in (10, 11)]
+    for vf, hb in tables:
+        trial(dict(best, visited_format=vf, hash_bits=hb))
+    for lpr in (2, 4, 8, 16, 32):
+        trial(dict(best, lanes_per_row=lpr))
     for wpb in (1, 2, 4):
         for pers in (False, True):
             trial(dict(best, warps_per_block=wpb, persistent=pers))
     trial(dict(best, lean=1))
+    # the table size again, at the chosen lane mapping and CTA shape
+    for vf, hb in tables:
+        trial(dict(best, visited_format=vf, hash_bits=hb))
     if verbose:
         for o, t, same in sorted(results, key=lambda r: r[1])[:10]:
             print("%8.3f ms  same=%s  %s" % (t, same, o))

@@ -711,6 +711,32 @@ def main():
                                "launch": opt_c}
             curve.append(point)
 
+    # the multi-expansion layer-0 step (kann_search_opts.expand = p): its own
+    # smallest ef with recall@10 >= 0.95, timed like the headline form
+    multi = []
+    if rank == 0 and not args.no_curve:
+        for p_exp in (2, 4):
+            def multi_recalls(e, p_exp=p_exp):
+                ids_m, _ = K_.kann_search_ex(idx16, Qd, K, e, rerank=-1, expand=p_exp)
+                torch.cuda.synchronize()
+                return {"recall": recall_at(ids_m.cpu().numpy(), gt)}
+
+            ef_m, _ = select_ef(multi_recalls, "recall")
+            kwm = dict(kw16, expand=p_exp)
+            for _ in range(3):
+                K_.kann_search_ex(idx16, Qd, K, ef_m, rerank=-1, **kwm)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+            e0.record()
+            for _ in range(10):
+                ids_m, _ = K_.kann_search_ex(idx16, Qd, K, ef_m, rerank=-1, **kwm)
+            e1.record()
+            torch.cuda.synchronize()
+            ms_m = e0.elapsed_time(e1) / 10
+            multi.append({"expand": p_exp, "ef": ef_m, "recall@10": recall_at(ids_m.cpu().numpy(), gt),
+                          "qps": N_QUERY / (ms_m / 1e3), "ms": ms_m,
+                          "vs_one_expansion_qps": N_QUERY / (ms_m / 1e3) / qps})
+
     serving = None
     if rank == 0 and world == 1 and not args.no_serving:
         serving = run_serving(g, Xd, Q, dev, args)
@@ -754,6 +780,7 @@ def main():
             "cpu_baseline": cpu_base,
             "serving": serving,
             "recall_qps_curve": curve,
+            "multi_expansion": multi,
         }
         print(json.dumps(out))
     if world > 1:

@@ -68,6 +68,7 @@ extern "C" {
 #define KANN_MAX_EF 1024    /* ef_eff = max(ef, k) must not exceed this */
 #define KANN_MAX_M0 64      /* layer-0 degree cap (M0 = 2M, so M <= 32) */
 #define KANN_MAX_DIM 4096   /* dense dimension */
+#define KANN_MAX_EXPAND 4   /* kann_search_opts.expand */
 
 /* ---- index descriptions -------------------------------------------------*/
 
@@ -186,6 +187,15 @@ typedef struct {
                               2 = wide: 32-bit id slots.  Both may forget ids (a forgotten id
                               is evaluated again), neither reports an unvisited id as visited,
                               so results do not depend on this choice */
+  int32_t expand;          /* dense indices: layer-0 entries expanded per step.  0 or 1 = the
+                              HNSW search step (one expansion, the parity form); 2..KANN_MAX_EXPAND
+                              = a batched variant that marks that many best unexpanded entries
+                              expanded at once, evaluates all their unvisited neighbours in one
+                              batch and keeps the ef best -- a different search (it may expand an
+                              entry the one-at-a-time step would evict first), with more rows in
+                              flight per dependent step; its results are defined by that rule,
+                              not by the one-expansion search.  PQ and sparse indices: KANN_EINVAL
+                              unless 0 or 1.  max_hops counts expansions */
 } kann_search_opts;
 
 /* HNSW K-NN-SEARCH (Malkov & Yashunin Alg. 5) for n dense FP32 queries

@@ -53,6 +53,7 @@ def lib():
             "orc_graph_import": [_i64, _i32, _i32, _i32, _i64, _p, _p, _p, _p],
             "orc_search_dense": [_p, _i32, _p, _p, _i32, _i32, _p, _i64, _i32, _i32, _i32, _i64, _i32,
                                  _p, _p, _p],
+            "orc_search_dense_multi": [_p, _i32, _p, _p, _i32, _i32, _p, _i64, _i32, _i32, _i32, _i32, _p, _p, _p],
             "orc_search_pq": [_p, _p, _p, _i32, _i32, _i32, _i32, _i32, _p, _i64, _i32, _i32, _i32, _i32, _p, _p,
                               _p],
             "orc_search_sparse": [_p, _p, _p, _p, _p, _p, _p, _i64, _i32, _i32, _i32, _i32, _p, _p, _p],
@@ -210,6 +211,20 @@ def search_dense(g, data, queries, k, ef, metric, dtype=DT_F32, scale=None, form
     cnt = np.empty((nq, 4), np.int64)
     lib().orc_search_dense(g.h, dtype, _ptr(data), _ptr(scale), d, metric, _ptr(queries), nq, k, ef, form,
                            visited_cap, nthreads, _ptr(ids), _ptr(dists), _ptr(cnt))
+    return ids, dists, cnt
+
+
+def search_dense_multi(g, data, queries, k, ef, metric, expand, dtype=DT_F32, scale=None, nthreads=0):
+    """Dense search whose layer-0 step expands the `expand` best unexpanded
+    entries at once (a batched variant, not HNSW's one-at-a-time step)."""
+    data = np.ascontiguousarray(data)
+    queries = _c(queries, np.float32)
+    nq, d = queries.shape
+    ids = np.empty((nq, k), np.int32)
+    dists = np.empty((nq, k), np.float64)
+    cnt = np.empty((nq, 4), np.int64)
+    lib().orc_search_dense_multi(g.h, dtype, _ptr(data), _ptr(scale), d, metric, _ptr(queries), nq, k, ef, expand,
+                                 nthreads, _ptr(ids), _ptr(dists), _ptr(cnt))
     return ids, dists, cnt
 
 

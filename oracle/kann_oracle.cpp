@@ -457,6 +457,52 @@ std::vector<Cand> search_layer_flags(const Graph& g, const Space& sp, Cand ep, i
   return W;
 }
 
+// Layer-0 search that expands the p best unexpanded entries of W per step
+// (a batched variant of the flag-buffer search above; it is not the search
+// of the HNSW paper, which expands one entry at a time, so for p > 1 its
+// results are not those of search_layer_flags).  A step marks the first p
+// unexpanded entries of W (in (d, id) order) expanded, evaluates every
+// neighbour of theirs that was not visited before (the lists in the order
+// of the chosen entries, each list in order), and inserts the new candidates
+// into W with the same bounded rule; the W after a step is the ef best of W
+// and the step's candidates, whatever the order within the step.  Stops when
+// W has no unexpanded entry.  The visited set is exact.
+std::vector<Cand> search_layer_multi(const Graph& g, const Space& sp, Cand ep, int ef, int p, int layer,
+                                     int64_t* n_dist, int64_t* n_exp) {
+  std::vector<Cand> W{ep};
+  std::vector<char> expanded{0};
+  std::unordered_set<int64_t> visited{ep.id};
+  for (;;) {
+    std::vector<int64_t> chosen;
+    for (size_t c = 0; c < W.size() && (int)chosen.size() < p; ++c) {
+      if (expanded[c]) continue;
+      expanded[c] = 1;
+      chosen.push_back(W[c].id);
+    }
+    if (chosen.empty()) break;
+    if (n_exp) *n_exp += (int64_t)chosen.size();
+    std::vector<Cand> fresh;
+    for (int64_t cid : chosen) {
+      for (int32_t e : g.nbrs(cid, layer)) {
+        if (e < 0 || visited.count(e)) continue;
+        visited.insert(e);
+        fresh.push_back(Cand{sp.qdist(e), e});
+        if (n_dist) ++*n_dist;
+      }
+    }
+    for (const Cand& ce : fresh) {
+      bool full = (int)W.size() >= ef;
+      if (full && !cand_less(ce, W.back())) continue;
+      size_t pos = std::lower_bound(W.begin(), W.end(), ce, CandLess()) - W.begin();
+      if (pos < W.size() && W[pos].id == ce.id) continue;
+      W.insert(W.begin() + pos, ce);
+      expanded.insert(expanded.begin() + pos, 0);
+      if ((int)W.size() > ef) { W.pop_back(); expanded.pop_back(); }
+    }
+  }
+  return W;
+}
+
 // Upper-layer descent, plain greedy form: move to the (d, id)-best
 // neighbour while it beats the current node; equals SEARCH-LAYER with ef=1.
 Cand greedy_layer(const Graph& g, const Space& sp, Cand cur, int layer, int64_t* n_dist, int64_t* n_hops) {
@@ -551,8 +597,10 @@ void build_graph(Graph& g, Space& sp, int64_t n, int M, int efC, uint64_t seed, 
 // flag-buffer layer-0 search (with an optionally forgetful visited set).
 // counters: [dist evals on layer 0, expansions on layer 0, dist evals on the
 // upper layers, upper-layer hops].
+// expand >= 1: the layer-0 search is search_layer_multi with that many
+// entries per step (upper layers as in form 1); 0: `form` decides.
 std::vector<Cand> knn_search(const Graph& g, const Space& sp, int k, int ef, int form,
-                             int64_t visited_cap, int64_t* counters) {
+                             int64_t visited_cap, int64_t* counters, int expand = 0) {
   int64_t c0 = 0, c1 = 0, c2 = 0, c3 = 0;
   std::vector<Cand> out;
   if (g.n > 0) {
@@ -567,8 +615,9 @@ std::vector<Cand> knn_search(const Graph& g, const Space& sp, int k, int ef, int
         ep = greedy_layer(g, sp, ep, lc, &c2, &c3);
       }
     }
-    std::vector<Cand> W = form == 0 ? search_layer_two_heap(g, sp, {ep}, efe, 0, &c0, &c1)
-                                    : search_layer_flags(g, sp, ep, efe, 0, visited_cap, &c0, &c1);
+    std::vector<Cand> W = expand >= 1 ? search_layer_multi(g, sp, ep, efe, expand, 0, &c0, &c1)
+                          : form == 0 ? search_layer_two_heap(g, sp, {ep}, efe, 0, &c0, &c1)
+                                      : search_layer_flags(g, sp, ep, efe, 0, visited_cap, &c0, &c1);
     for (int i = 0; i < k && i < (int)W.size(); ++i) out.push_back(W[i]);
   }
   if (counters) {
@@ -728,6 +777,24 @@ void orc_search_dense(const void* gp, int dtype, const void* data, const float* 
     for (int64_t qi = 0; qi < nq; ++qi) {
       sp.set_query(queries + (size_t)qi * d);
       std::vector<Cand> r = knn_search(g, sp, k, ef, form, visited_cap, counters ? counters + qi * 4 : nullptr);
+      write_results(r, k, ids + qi * k, dists + qi * k);
+    }
+  }
+}
+
+// Dense search whose layer-0 step expands `expand` entries at once
+// (search_layer_multi); the upper layers descend greedily.
+void orc_search_dense_multi(const void* gp, int dtype, const void* data, const float* scale, int d, int metric,
+                            const float* queries, int64_t nq, int k, int ef, int expand, int nthreads, int32_t* ids,
+                            double* dists, int64_t* counters) {
+  const Graph& g = *(const Graph*)gp;
+#pragma omp parallel num_threads(threads_or_default(nthreads))
+  {
+    DenseSpace sp(dtype, data, scale, d, metric);
+#pragma omp for schedule(dynamic, 1)
+    for (int64_t qi = 0; qi < nq; ++qi) {
+      sp.set_query(queries + (size_t)qi * d);
+      std::vector<Cand> r = knn_search(g, sp, k, ef, 1, 0, counters ? counters + qi * 4 : nullptr, expand);
       write_results(r, k, ids + qi * k, dists + qi * k);
     }
   }

@@ -48,6 +48,7 @@ struct SearchArgs {
   int lean;              // dense: half the rows in flight, 64-register budget
   int lut16;             // PQ: per-query table in FP16 with a power-of-two scale
   int efcap;       // W capacity (efmax rounded up to a multiple of 32)
+  int expand;      // layer-0 entries expanded per step (1 = the HNSW step; 2..KANN_MAX_EXPAND: batched)
   int warp_smem;   // bytes of shared memory per warp
 };
 
@@ -72,15 +73,24 @@ typedef void (*SearchKernelFn)(const SearchArgs);
 
 // Dense search kernel of one storage format for `cplt` chunks per lane
 // (kann_search_{f32,f16,bf16,e4m3}.cu); lpr_exact > 0 when a row is exactly
-// lpr_exact * cplt chunks.  Null when no kernel exists for the settings.
+// lpr_exact * cplt chunks; the _multi pickers give the multi-expansion
+// kernels.  Null when no kernel exists for the settings.
 SearchKernelFn pick_search_f32(int cplt, bool lean, int metric, int lpr_exact);
 SearchKernelFn pick_search_f16(int cplt, bool lean, int metric, int lpr_exact);
 SearchKernelFn pick_search_bf16(int cplt, bool lean, int metric, int lpr_exact);
 SearchKernelFn pick_search_e4m3(int cplt, bool lean, int metric, int lpr_exact);
+SearchKernelFn pick_search_f32_multi(int cplt, int metric, int lpr_exact);
+SearchKernelFn pick_search_f16_multi(int cplt, int metric, int lpr_exact);
+SearchKernelFn pick_search_bf16_multi(int cplt, int metric, int lpr_exact);
+SearchKernelFn pick_search_e4m3_multi(int cplt, int metric, int lpr_exact);
+
+// Candidate keys a warp keeps per step: 64 per expanded entry, plus 64 for
+// the ranked survivors of a batch when several entries are expanded at once.
+__host__ __device__ constexpr int cand_keys(int expand) { return 64 * expand + (expand > 1 ? 64 : 0); }
 
 // Per-warp shared memory needed by a dense search with these settings
 // (compact: a visited table of 16-bit slots, else 32-bit).
-int search_warp_smem(int efcap, int hbits, bool compact);
+int search_warp_smem(int efcap, int hbits, bool compact, int expand = 1);
 int search_warp_smem_pq(int efcap, int hbits, bool compact, int m, bool lut16 = false);
 // Shared memory of a PQ search team's control block (after the query's region).
 constexpr int PQ_TEAM_CTL_BYTES = 64;

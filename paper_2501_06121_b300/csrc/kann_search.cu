@@ -40,8 +40,8 @@ int pow2_at_least(int x) {
 
 }  // namespace
 
-int search_warp_smem(int efcap, int hbits, bool compact) {
-  return efcap * 8 + 64 * 8 + 64 * 4 + ((compact ? 2 : 4) << hbits);
+int search_warp_smem(int efcap, int hbits, bool compact, int expand) {
+  return efcap * 8 + cand_keys(expand) * 8 + 64 * expand * 4 + ((compact ? 2 : 4) << hbits);
 }
 
 int launch_search_dense(const SearchArgs& a, int dtype, int wpb, void* stream) {
@@ -50,10 +50,20 @@ int launch_search_dense(const SearchArgs& a, int dtype, int wpb, void* stream) {
   const int lpr_exact = a.nchunks == a.lpr * cplt ? a.lpr : 0;
   SearchKernelFn fn = nullptr;
   switch (dtype) {
-    case KANN_F32: fn = pick_search_f32(cplt, a.lean, a.metric, lpr_exact); break;
-    case KANN_F16: fn = pick_search_f16(cplt, a.lean, a.metric, lpr_exact); break;
-    case KANN_BF16: fn = pick_search_bf16(cplt, a.lean, a.metric, lpr_exact); break;
-    case KANN_E4M3: fn = pick_search_e4m3(cplt, a.lean, a.metric, lpr_exact); break;
+    case KANN_F32:
+      fn = a.expand > 1 ? pick_search_f32_multi(cplt, a.metric, lpr_exact) : pick_search_f32(cplt, a.lean, a.metric, lpr_exact);
+      break;
+    case KANN_F16:
+      fn = a.expand > 1 ? pick_search_f16_multi(cplt, a.metric, lpr_exact) : pick_search_f16(cplt, a.lean, a.metric, lpr_exact);
+      break;
+    case KANN_BF16:
+      fn = a.expand > 1 ? pick_search_bf16_multi(cplt, a.metric, lpr_exact)
+                        : pick_search_bf16(cplt, a.lean, a.metric, lpr_exact);
+      break;
+    case KANN_E4M3:
+      fn = a.expand > 1 ? pick_search_e4m3_multi(cplt, a.metric, lpr_exact)
+                        : pick_search_e4m3(cplt, a.lean, a.metric, lpr_exact);
+      break;
     default: break;
   }
   if (!fn) return (int)cudaErrorInvalidValue;

@@ -160,9 +160,11 @@ __device__ __forceinline__ int count_le(const int* A, int n, int x) {
   return lo;
 }
 
-// Shared memory of one warp: W[efcap] keys, candidate keys[64], candidate
-// ids[64] (which also hold the survivors' W-ranks once the step's distances
-// are done: the two are never live together), then the visited table
+// Shared memory of one warp: W[efcap] keys, candidate keys[64] (with
+// multi-expansion 64 per expanded entry plus 64 for the ranked survivors),
+// candidate ids[64 per expanded entry] (which also hold the survivors'
+// W-ranks once the step's distances are done: the two are never live
+// together), then the visited table
 // (2^hbits slots of 2 bytes, compact, or 4 bytes, wide), then back-end scratch.
 struct WarpSmem {
   u64* W;
@@ -171,16 +173,20 @@ struct WarpSmem {
   int* clb;
   uint32_t* H;
   unsigned char* extra;
-  __device__ __forceinline__ WarpSmem(unsigned char* ws, int efcap, int hbits, bool compact) {
+  __device__ __forceinline__ WarpSmem(unsigned char* ws, int efcap, int hbits, bool compact, int expand) {
     W = reinterpret_cast<u64*>(ws);
     ck = W + efcap;
-    cid = reinterpret_cast<int*>(ck + 64);
+    cid = reinterpret_cast<int*>(ck + cand_keys(expand));
     clb = cid;
-    H = reinterpret_cast<uint32_t*>(cid + 64);
+    H = reinterpret_cast<uint32_t*>(cid + 64 * expand);
     extra = reinterpret_cast<unsigned char*>(H) + ((compact ? 2 : 4) << hbits);
   }
-  __device__ __forceinline__ WarpSmem(unsigned char* ws, const SearchArgs& a)
-      : WarpSmem(ws, a.efcap, a.hbits, a.vis_r >= 0) {}
+  // one-expansion kernels (MULTI false) lay the area out for one expansion
+  // at compile time; a multi-expansion kernel reads a.expand
+  template <bool MULTI = false>
+  __device__ __forceinline__ static WarpSmem of(unsigned char* ws, const SearchArgs& a) {
+    return WarpSmem(ws, a.efcap, a.hbits, a.vis_r >= 0, MULTI ? a.expand : 1);
+  }
 };
 
 enum { TEAM_DIST = 1, TEAM_RERANK = 2, TEAM_DONE = 3 };
@@ -388,7 +394,7 @@ struct PQBackend {
   // The same table built by a team of T warps (thread t of the team takes
   // entries t, t + 32 T, ...); ends with the team at barrier 1.
   __device__ void init_team(const SearchArgs& a, int qi, int lane, int w, int T, unsigned char* ws, TeamCtl* tc) {
-    WarpSmem s(ws, a);
+    const WarpSmem s = WarpSmem::of(ws, a);
     lut = reinterpret_cast<LutT*>(s.extra);
     const int m = a.pq_m;
     const float* q = a.q + (size_t)qi * m * a.pq_dsub;
@@ -665,7 +671,7 @@ __device__ __noinline__ int rerank_phase(const unsigned char* rr, int rr_dtype, 
 
 // Clear the visited table and put W's ids back (cold path); returns the
 // number of ids stored.
-__device__ __noinline__ int reset_visited(const Visited& V, const u64* W, int len, int lane) {
+__device__ __noinline__ int reset_visited(const Visited V, const u64* W, int len, int lane) {
   V.clear(lane);
   __syncwarp();
   int n = 0;
@@ -706,16 +712,188 @@ __device__ __noinline__ int order_by_sort(u64 e0, u64 e1, bool k0, bool k1, cons
   return cs0 + __popc(s1);
 }
 
+// Merge a batch of up to 64 candidate keys (two per lane, KEY_MAX = none)
+// into W: the survivors are the keys that beat worst(W) and are not in W
+// already; they are ranked (by counting, or by a sorting network when there
+// are many or some repeat), W[lo..len) is moved right by the number of
+// survivors ranked before each entry, last chunk first, and the survivors are
+// dropped in place.  ck_out / clb receive the ranked survivors and their
+// W-ranks (64 entries each).  The result is the ef best of W and the batch.
+__device__ __forceinline__ void merge_batch(u64 e0, u64 e1, u64* W, int& len, int ef, int& cursor, u64* ck_out,
+                                            int* clb, int lane) {
+  const u64 worst = len >= ef ? kmask(W[len - 1]) : KEY_MAX;
+  bool k0 = e0 < worst, k1 = e1 < worst;
+  int lb0 = 0, lb1 = 0;
+  if (k0) {
+    lb0 = lower_bound_w(W, len, e0);
+    k0 = !(lb0 < len && kmask(W[lb0]) == e0);
+  }
+  if (k1) {
+    lb1 = lower_bound_w(W, len, e1);
+    k1 = !(lb1 < len && kmask(W[lb1]) == e1);
+  }
+  const unsigned s0 = __ballot_sync(FULL, k0), s1 = __ballot_sync(FULL, k1);
+  const int c = __popc(s0) + __popc(s1);
+  if (c == 0) return;
+  int cnew = 0;
+  bool sorted = false;
+  if (c <= 16) {
+    // rank of a survivor = number of survivors with a smaller key
+    int r0 = 0, r1 = 0;
+    bool d0 = false, d1 = false;
+    for (unsigned m = s0; m; m &= m - 1) {
+      const int src = __ffs(m) - 1;
+      const u64 x = __shfl_sync(FULL, e0, src);
+      r0 += x < e0;
+      r1 += x < e1;
+      d0 |= (x == e0) && (src < lane);
+      d1 |= x == e1;
+    }
+    for (unsigned m = s1; m; m &= m - 1) {
+      const int src = __ffs(m) - 1;
+      const u64 x = __shfl_sync(FULL, e1, src);
+      r0 += x < e0;
+      r1 += x < e1;
+      d1 |= (x == e1) && (src < lane);
+    }
+    // a key repeated inside the batch (possible only after the visited
+    // table forgot, with a repeated edge) takes the sorting path
+    if (__ballot_sync(FULL, (k0 && d0) || (k1 && d1)) == 0) {
+      __syncwarp();
+      if (k0) {
+        ck_out[r0] = e0;
+        clb[r0] = lb0;
+      }
+      if (k1) {
+        ck_out[r1] = e1;
+        clb[r1] = lb1;
+      }
+      cnew = c;
+      sorted = true;
+    }
+  }
+  if (!sorted) cnew = order_by_sort(e0, e1, k0, k1, W, len, ck_out, clb, lane);
+  __syncwarp();
+  const int lo = clb[0];
+  for (int top = len; top > lo; top -= 32) {
+    const int i = top - 32 + lane;
+    const bool act = i >= lo;
+    u64 val = 0;
+    int dest = 0;
+    if (act) {
+      val = W[i];
+      dest = i + count_le(clb, cnew, i);
+    }
+    __syncwarp();
+    if (act && dest < ef) W[dest] = val;
+    __syncwarp();
+  }
+  for (int j = lane; j < cnew; j += 32) {
+    const int pos = j + clb[j];
+    if (pos < ef) W[pos] = ck_out[j];
+  }
+  __syncwarp();
+  len = min(len + cnew, ef);
+  if (lo < cursor) cursor = lo;
+}
+
 template <class B>
 __device__ __forceinline__ uint32_t backend_status(const B&) { return 0u; }
 __device__ __forceinline__ uint32_t backend_status(const SparseBackend& b) {
   return b.trunc ? KANN_QSTAT_QUERY_TRUNCATED : 0u;
 }
 
-template <class B, int T = 1>
+// One step of the multi-expansion layer-0 search (a batched variant of the
+// HNSW step, under its own oracle form; not the parity search): the
+// min(a.expand, remaining hop budget) best unexpanded entries of W are
+// marked expanded together, their adjacency rows read at once, their
+// unvisited neighbours evaluated in one batch of up to 64 * a.expand rows,
+// and the batch merged into W 64 keys at a time (the bounded top-ef merge
+// does not depend on order).  More rows are in flight per dependent step
+// than with one expansion.  Returns false when W has no unexpanded entry or
+// the hop cap is reached.
+template <int T, class B>
+__device__ __forceinline__ bool multi_step(const SearchArgs& a, B& be, u64* W, u64* ck, int* cid, int* clb,
+                                           const Visited& V, int& len, int ef, int& cursor, int& hops, int& stored,
+                                           uint32_t& st, int& c_l0d, int& c_l0e, int lane, TeamCtl* tc) {
+  const unsigned lt = (1u << lane) - 1u;
+  const int P = a.expand;
+  int s0 = -1, s1 = -1, s2 = -1, s3 = -1, ns = 0;
+  for (int b = cursor; b < len && ns < P; b += 32) {
+    const int i = b + lane;
+    const bool un = i < len && !(W[i] & FLAG);
+    unsigned m = __ballot_sync(FULL, un);
+    while (m != 0u && ns < P) {
+      const int pos = b + __ffs(m) - 1;
+      m &= m - 1;
+      if (ns == 0) s0 = pos;
+      else if (ns == 1) s1 = pos;
+      else if (ns == 2) s2 = pos;
+      else s3 = pos;
+      ++ns;
+    }
+  }
+  if (ns == 0) return false;
+  if (hops >= a.max_hops) {
+    st |= KANN_QSTAT_HOPCAP;
+    return false;
+  }
+  if (ns > a.max_hops - hops) ns = a.max_hops - hops;
+  hops += ns;
+  c_l0e += ns;
+  const int sel[4] = {s0, s1, s2, s3};
+  int ids[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) ids[j] = j < ns ? (int)key_id(W[sel[j]]) : -1;
+  __syncwarp();
+  if (lane == 0) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      if (j < ns) W[sel[j]] |= FLAG;
+  }
+  cursor = (ns == 1 ? s0 : ns == 2 ? s1 : ns == 3 ? s2 : s3) + 1;
+  int v[8];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int32_t* nb = a.l0 + (int64_t)(ids[j] < 0 ? 0 : ids[j]) * a.M0;
+    v[2 * j] = (j < ns && lane < a.M0) ? __ldg(nb + lane) : -1;
+    v[2 * j + 1] = (j < ns && lane + 32 < a.M0) ? __ldg(nb + 32 + lane) : -1;
+  }
+  int cnt = 0;
+  bool forgot = false, bad = false;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    int vj = v[j];
+    bad |= vj >= a.n;
+    if (vj >= a.n) vj = -1;
+    const int r = vj >= 0 ? V.insert((uint32_t)vj) : 0;
+    forgot |= r == 2;
+    stored += __popc(__ballot_sync(FULL, r == 1));
+    const unsigned bm = __ballot_sync(FULL, r != 0);
+    if (r) cid[cnt + __popc(bm & lt)] = vj;
+    cnt += __popc(bm);
+  }
+  if (forgot) st |= KANN_QSTAT_FORGOT;
+  if (bad) st |= KANN_QSTAT_BAD_ID;
+  __syncwarp();
+  if (cnt == 0) return true;
+  team_dists<T>(be, a, cid, cnt, ck, lane, tc);
+  __syncwarp();
+  c_l0d += cnt;
+  u64* ck_out = ck + 64 * a.expand;  // past every candidate key of the batch
+  for (int off = 0; off < cnt; off += 64) {
+    const u64 e0 = off + lane < cnt ? ck[off + lane] : KEY_MAX;
+    const u64 e1 = off + lane + 32 < cnt ? ck[off + lane + 32] : KEY_MAX;
+    __syncwarp();
+    merge_batch(e0, e1, W, len, ef, cursor, ck_out, clb, lane);
+  }
+  return true;
+}
+
+template <class B, int T = 1, bool MULTI = false>
 __device__ __forceinline__ void search_one(const SearchArgs& a, B& be, int qi, int lane, unsigned char* ws,
                                            TeamCtl* tc = nullptr) {
-  WarpSmem s(ws, a);
+  const WarpSmem s = WarpSmem::of<MULTI>(ws, a);
   u64* W = s.W;
   u64* ck = s.ck;
   int* cid = s.cid;
@@ -779,6 +957,15 @@ __device__ __forceinline__ void search_one(const SearchArgs& a, B& be, int qi, i
   __syncwarp();
   int len = 1, cursor = 0, hops = 0, stored = 1;
   for (;;) {
+    if constexpr (MULTI) {
+      if (!multi_step<T>(a, be, W, ck, cid, clb, V, len, ef, cursor, hops, stored, st, c_l0d, c_l0e, lane, tc))
+        break;
+      if (stored > V.limit()) {
+        st |= KANN_QSTAT_FORGOT;
+        stored = reset_visited(V, W, len, lane);
+      }
+      continue;
+    }
     int p = -1;
     for (int b = cursor; b < len; b += 32) {
       const int i = b + lane;
@@ -820,7 +1007,9 @@ __device__ __forceinline__ void search_one(const SearchArgs& a, B& be, int qi, i
       team_dists<T>(be, a, cid, cnt, ck, lane, tc);
       __syncwarp();
       c_l0d += cnt;
-      // survivors: keys that beat worst(W) and are not in W already
+      // survivors: keys that beat worst(W) and are not in W already (the
+      // merge of merge_batch, written out here for the one-expansion step,
+      // whose register allocation it keeps)
       const u64 worst = len >= ef ? kmask(W[len - 1]) : KEY_MAX;
       const u64 e0 = lane < cnt ? ck[lane] : KEY_MAX;
       const u64 e1 = lane + 32 < cnt ? ck[lane + 32] : KEY_MAX;
@@ -840,7 +1029,6 @@ __device__ __forceinline__ void search_one(const SearchArgs& a, B& be, int qi, i
       if (c > 0) {
         bool sorted = false;
         if (c <= 16) {
-          // rank of a survivor = number of survivors with a smaller key
           int r0 = 0, r1 = 0;
           bool d0 = false, d1 = false;
           for (unsigned m = s0; m; m &= m - 1) {
@@ -858,8 +1046,6 @@ __device__ __forceinline__ void search_one(const SearchArgs& a, B& be, int qi, i
             r1 += x < e1;
             d1 |= (x == e1) && (src < lane);
           }
-          // a key repeated inside the batch (possible only after the visited
-          // table forgot, with a repeated edge) takes the sorting path
           if (__ballot_sync(FULL, (k0 && d0) || (k1 && d1)) == 0) {
             __syncwarp();
             if (k0) {
@@ -876,8 +1062,6 @@ __device__ __forceinline__ void search_one(const SearchArgs& a, B& be, int qi, i
         }
         if (!sorted) cnew = order_by_sort(e0, e1, k0, k1, W, len, ck, clb, lane);
         __syncwarp();
-        // merge: move W[lo..len) right by the number of survivors ranked before
-        // each entry, last chunk first, then drop the survivors in place
         const int lo = clb[0];
         for (int top = len; top > lo; top -= 32) {
           const int i = top - 32 + lane;
@@ -954,14 +1138,14 @@ struct MinBlocks {
 // b * warps + w; the persistent form has every warp take the next query index
 // from a device counter until the batch is exhausted (work stealing: a warp
 // that finishes a cheap query starts the next one at once).
-template <class B>
+template <class B, bool MULTI = false>
 __device__ __forceinline__ void run_queries(const SearchArgs& a, B& be) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   unsigned char* ws = smem + (size_t)warp * a.warp_smem;
   if (a.work_counter == nullptr) {
     const int qi = blockIdx.x * (blockDim.x >> 5) + warp;
-    if (qi < a.nq) search_one<B>(a, be, qi, lane, ws);
+    if (qi < a.nq) search_one<B, 1, MULTI>(a, be, qi, lane, ws);
     return;
   }
   int nq = a.nq;
@@ -971,7 +1155,7 @@ __device__ __forceinline__ void run_queries(const SearchArgs& a, B& be) {
     if (lane == 0) qi = atomicAdd(a.work_counter, 1);
     qi = __shfl_sync(FULL, qi, 0);
     if (qi >= nq) break;
-    search_one<B>(a, be, qi, lane, ws);
+    search_one<B, 1, MULTI>(a, be, qi, lane, ws);
   }
 }
 
@@ -979,7 +1163,7 @@ __device__ __forceinline__ void run_queries(const SearchArgs& a, B& be) {
 template <int T, class B>
 __device__ __forceinline__ void team_helper(const SearchArgs& a, B& be, int qi, int lane, int w, unsigned char* ws,
                                             TeamCtl* tc) {
-  WarpSmem s(ws, a);  // warp 0's candidate ids and keys
+  const WarpSmem s = WarpSmem::of(ws, a);  // warp 0's candidate ids and keys
   for (;;) {
     team_bar(T);
     const int cmd = tc->cmd, cnt = tc->cnt;
@@ -1035,10 +1219,10 @@ __device__ __forceinline__ void run_queries_team(const SearchArgs& a, B& be) {
   }
 }
 
-template <int DT, int CPLT, bool LEAN, int MET, int LPR>
+template <int DT, int CPLT, bool LEAN, int MET, int LPR, bool MULTI = false>
 __global__ void __launch_bounds__(128, MinBlocks<DT, CPLT, LEAN>::value) search_dense_kernel(const SearchArgs a) {
   DenseBackend<DT, CPLT, LEAN, MET, LPR> be;
-  run_queries(a, be);
+  run_queries<decltype(be), MULTI>(a, be);
 }
 
 constexpr int PQ_TEAM = 8;  // warps sharing one query's lookup table (TeamCtl::wmax holds 8)
@@ -1049,26 +1233,26 @@ __global__ void __launch_bounds__(PQ_TEAM * 32, 1) search_pq_kernel(const Search
   run_queries_team<PQ_TEAM>(a, be);
 }
 
-template <int DT, int MET>
+template <int DT, int MET, bool MULTI = false>
 SearchKernelFn pick_general(int cplt, bool lean) {
   switch (cplt * 2 + (lean ? 1 : 0)) {
-    case 2: return search_dense_kernel<DT, 1, false, MET, 0>;
-    case 4: return search_dense_kernel<DT, 2, false, MET, 0>;
-    case 5: return search_dense_kernel<DT, 2, true, MET, 0>;
-    case 8: return search_dense_kernel<DT, 4, false, MET, 0>;
-    case 16: return search_dense_kernel<DT, 8, false, MET, 0>;
+    case 2: return search_dense_kernel<DT, 1, false, MET, 0, MULTI>;
+    case 4: return search_dense_kernel<DT, 2, false, MET, 0, MULTI>;
+    case 5: return MULTI ? nullptr : search_dense_kernel<DT, 2, true, MET, 0>;
+    case 8: return search_dense_kernel<DT, 4, false, MET, 0, MULTI>;
+    case 16: return search_dense_kernel<DT, 8, false, MET, 0, MULTI>;
     default: return nullptr;
   }
 }
 
-template <int DT, int CPLT, bool LEAN, int MET>
+template <int DT, int CPLT, bool LEAN, int MET, bool MULTI = false>
 SearchKernelFn pick_exact(int lpr) {
   switch (lpr) {
-    case 2: return search_dense_kernel<DT, CPLT, LEAN, MET, 2>;
-    case 4: return search_dense_kernel<DT, CPLT, LEAN, MET, 4>;
-    case 8: return search_dense_kernel<DT, CPLT, LEAN, MET, 8>;
-    case 16: return search_dense_kernel<DT, CPLT, LEAN, MET, 16>;
-    case 32: return search_dense_kernel<DT, CPLT, LEAN, MET, 32>;
+    case 2: return search_dense_kernel<DT, CPLT, LEAN, MET, 2, MULTI>;
+    case 4: return search_dense_kernel<DT, CPLT, LEAN, MET, 4, MULTI>;
+    case 8: return search_dense_kernel<DT, CPLT, LEAN, MET, 8, MULTI>;
+    case 16: return search_dense_kernel<DT, CPLT, LEAN, MET, 16, MULTI>;
+    case 32: return search_dense_kernel<DT, CPLT, LEAN, MET, 32, MULTI>;
     default: return nullptr;
   }
 }
@@ -1076,6 +1260,20 @@ SearchKernelFn pick_exact(int lpr) {
 // Dense kernel of one storage format: the exact-tiling form when the launch's
 // rows are lpr_exact * cplt chunks with cplt the format's default chunks per
 // lane (the lean form exists for two chunks per lane), else the general form.
+// Multi-expansion kernel of one storage format (no lean variant): the
+// exact-tiling form at the format's default chunks per lane, else the
+// general form.  Instantiated in kann_search_{f32,f16,bf16,e4m3}_multi.cu.
+template <int DT>
+SearchKernelFn pick_dense_multi_t(int cplt, int metric, int lpr_exact) {
+  constexpr int CX = default_chunks_per_lane(DT);
+  SearchKernelFn f = nullptr;
+  if (lpr_exact > 0 && cplt == CX)
+    f = metric == KANN_L2 ? pick_exact<DT, CX, false, KANN_L2, true>(lpr_exact)
+                          : pick_exact<DT, CX, false, KANN_IP, true>(lpr_exact);
+  if (!f) f = metric == KANN_L2 ? pick_general<DT, KANN_L2, true>(cplt, false) : pick_general<DT, KANN_IP, true>(cplt, false);
+  return f;
+}
+
 template <int DT>
 SearchKernelFn pick_dense_t(int cplt, bool lean, int metric, int lpr_exact) {
   constexpr int CX = default_chunks_per_lane(DT);

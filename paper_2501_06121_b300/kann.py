@@ -20,6 +20,7 @@ KANN_L2, KANN_IP = 0, 1
 KANN_F32, KANN_F16, KANN_BF16, KANN_E4M3 = 0, 1, 2, 3
 KANN_QSTAT_HOPCAP, KANN_QSTAT_FORGOT, KANN_QSTAT_BAD_ID, KANN_QSTAT_QUERY_TRUNCATED = 1, 2, 4, 8
 KANN_MAX_EF = 1024
+KANN_MAX_EXPAND = 4
 
 _TORCH_DTYPE = {KANN_F32: torch.float32, KANN_F16: torch.float16, KANN_BF16: torch.bfloat16,
                 KANN_E4M3: torch.uint8}
@@ -63,7 +64,7 @@ class kann_search_opts(ctypes.Structure):
                 ("pq_lut_f16", ctypes.c_int32),
                 ("d_status", ctypes.c_void_p), ("d_counters", ctypes.c_void_p),
                 ("d_work_counter", ctypes.c_void_p), ("d_n", ctypes.c_void_p),
-                ("visited_format", ctypes.c_int32)]
+                ("visited_format", ctypes.c_int32), ("expand", ctypes.c_int32)]
 
 
 _L = None
@@ -211,12 +212,13 @@ KANN_VISITED_AUTO, KANN_VISITED_COMPACT, KANN_VISITED_WIDE = 0, 1, 2
 
 
 def _opts(rerank=0, max_hops=0, hash_bits=0, warps_per_block=0, lanes_per_row=0, status=None, counters=None,
-          work_counter=None, n_device=None, lean=0, pq_lut_f16=0, visited_format=0):
+          work_counter=None, n_device=None, lean=0, pq_lut_f16=0, visited_format=0, expand=0):
     _require_cuda(status, counters, work_counter, n_device)
     p = lambda t: t.data_ptr() if t is not None else None
     return kann_search_opts(int(rerank), int(max_hops), int(hash_bits), int(warps_per_block), int(lanes_per_row),
                             int(lean), int(pq_lut_f16),
-                            p(status), p(counters), p(work_counter), p(n_device), int(visited_format))
+                            p(status), p(counters), p(work_counter), p(n_device), int(visited_format),
+                            int(expand))
 
 
 def kann_search(index, queries, k, ef, ids=None, dists=None, stream=None):

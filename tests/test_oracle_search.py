@@ -114,3 +114,65 @@ def test_nan_query_does_not_fail():
     q = np.full((1, 4), np.nan, np.float32)
     ids, d, _ = O.search_dense(g, X, q, 5, 10, O.L2)
     assert np.all(np.isnan(d)) and np.all(ids >= 0)
+
+
+# ------------------------------------------------------------------ multi-expansion form
+def test_multi_expansion_hand_worked_golden():
+    gold = load_golden("hand_search.json")
+    multi = load_golden("hand_search_multi.json")
+    cases = {c["name"]: c for c in gold["cases"]}
+    for mc in multi["cases"]:
+        case = cases[mc["name"]]
+        g = O.import_graph(golden_graph(case))
+        X = np.array(case["x"], np.float32).reshape(-1, 1)
+        q = np.array([[case["q"]]], np.float32)
+        for run in mc["runs"]:
+            ids, d, cnt = O.search_dense_multi(g, X, q, run["k"], run["ef"], O.L2, multi["p"])
+            assert ids[0].tolist() == run["ids"], (mc["name"], run)
+            assert d[0].tolist() == run["dists"]
+            assert cnt[0].tolist() == run["counters"]
+
+
+def test_multi_expansion_with_one_entry_per_step_is_the_flag_search():
+    # p = 1: the batched step reduces to the one-at-a-time step (the merge of
+    # a whole neighbour list at once is the bounded top-ef insertion, which
+    # does not depend on order): same ids, distances and work counts
+    rng = np.random.default_rng(23)
+    X = rng.integers(0, 50, (2500, 16)).astype(np.float32)
+    Q = rng.integers(0, 50, (120, 16)).astype(np.float32)
+    g = O.build_dense(X, O.L2, 10, 60, 23)
+    for ef in (10, 40, 150):
+        a = O.search_dense(g, X, Q, 10, ef, O.L2)
+        b = O.search_dense_multi(g, X, Q, 10, ef, O.L2, 1)
+        for x, y in zip(a, b):
+            assert np.array_equal(x, y), ef
+
+
+@pytest.mark.parametrize("p", [2, 4])
+def test_multi_expansion_brute_force_when_ef_covers_n(p):
+    rng = np.random.default_rng(29)
+    X = rng.standard_normal((400, 8)).astype(np.float32)
+    Q = rng.standard_normal((40, 8)).astype(np.float32)
+    g = O.build_dense(X, O.L2, 8, 50, 5)
+    ids, d, cnt = O.search_dense_multi(g, X, Q, 10, 400, O.L2, p)
+    ei, ed = O.exact_dense(X, Q, 10, O.L2)
+    assert recall(ids, ei, 10) == 1.0
+    assert np.allclose(d, ed, rtol=1e-12)
+    # with ef >= n every reachable node is evaluated and expanded exactly once
+    assert np.all(cnt[:, 1] == cnt[:, 0] + 1)
+
+
+@pytest.mark.parametrize("p", [2, 3, 4])
+def test_multi_expansion_recall_near_the_one_at_a_time_search(p):
+    # the batched step is a different search (not HNSW's): it may expand an
+    # entry that the one-at-a-time step would evict first, so it does at
+    # least as much work and finds a superset-or-equal quality W in practice
+    from paper_2501_06121_b300 import datagen as G
+    X, Q = G.gaussian_mixture(6000, 300, d=32, clusters=16, sigma=5.0, seed=31)
+    g = O.build_dense(X, O.L2, 12, 80, 31)
+    ei, _ = O.exact_dense(X, Q, 10, O.L2)
+    for ef in (16, 32, 64):
+        a = O.search_dense(g, X, Q, 10, ef, O.L2)
+        b = O.search_dense_multi(g, X, Q, 10, ef, O.L2, p)
+        assert recall(b[0], ei, 10) >= recall(a[0], ei, 10) - 0.005, (p, ef)
+        assert b[2][:, 1].sum() >= a[2][:, 1].sum()

@@ -409,18 +409,22 @@ def run_pq768(args, n=None, concentration=None):
 
     rows = []
     for k in (10, 100):
-        for ef in (128, 256, 512, 1024):
-            if ef < k:
+        for ef in (32, 64, 128, 256, 512, 1024):
+            if ef < k or (k > 10 and ef < 128):
                 continue
             ms, (ids, _) = timed(lambda: K_.kann_search_ex(idx_pq, Qd, k, ef, rerank=100 if k <= 100 else -1))
             r = recall_at(ids.cpu().numpy(), gt100, k)
             ms16, (ids16, _) = timed(lambda: K_.kann_search_ex(idx_pq, Qd, k, ef, rerank=100 if k <= 100 else -1,
-                                                               pq_lut_f16=1))
+                                                               pq_lut=K_.KANN_PQ_LUT_F16))
             r16 = recall_at(ids16.cpu().numpy(), gt100, k)
+            ms8, (ids8, _) = timed(lambda: K_.kann_search_ex(idx_pq, Qd, k, ef, rerank=100 if k <= 100 else -1,
+                                                             pq_lut=K_.KANN_PQ_LUT_U8))
+            r8 = recall_at(ids8.cpu().numpy(), gt100, k)
             ms32, (ids32, _) = timed(lambda: K_.kann_search_ex(idx32, Qd, k, ef))
             r32 = recall_at(ids32.cpu().numpy(), gt100, k)
             rows.append({"k": k, "ef": ef, "pq_rerank100_qps": 1e4 / (ms / 1e3), "pq_rerank100_recall": r,
                          "pq_f16table_rerank100_qps": 1e4 / (ms16 / 1e3), "pq_f16table_rerank100_recall": r16,
+                         "pq_u8table_rerank100_qps": 1e4 / (ms8 / 1e3), "pq_u8table_rerank100_recall": r8,
                          "fp32_qps": 1e4 / (ms32 / 1e3), "fp32_recall": r32})
             print(json.dumps(rows[-1]), flush=True)
     out = {"workload": "pq768", "n": n, "concentration": concentration,

@@ -60,6 +60,10 @@ extern "C" {
 #define KANN_BF16 2  /* bfloat16, round-to-nearest-even from FP32 */
 #define KANN_E4M3 3  /* OCP FP8 E4M3 with a per-vector FP32 scale s: x = s * code */
 
+#define KANN_PQ_LUT_F32 0       /* kann_search_opts.pq_lut */
+#define KANN_PQ_LUT_F16 1
+#define KANN_PQ_LUT_U8 2
+
 #define KANN_VISITED_AUTO 0     /* kann_search_opts.visited_format */
 #define KANN_VISITED_COMPACT 1
 #define KANN_VISITED_WIDE 2
@@ -164,11 +168,17 @@ typedef struct {
   int32_t lean;            /* dense rows of 2 chunks per lane: 1 = half the row batches in
                               flight for a 64-register budget (more warps per SM), -1 = off,
                               0 = automatic (off) */
-  int32_t pq_lut_f16;      /* PQ index only: 1 = per-query table held in FP16 (entries scaled by
-                              the power of two that brings the largest |entry| to at most
-                              2^15, rounded to nearest; each row's FP32 sum scaled back): half
-                              the shared memory, so twice the queries per SM at m = 192.
-                              0 = FP32 table */
+  int32_t pq_lut;          /* PQ index only: the per-query table's format.
+                              KANN_PQ_LUT_F32 (0): FP32 entries.
+                              KANN_PQ_LUT_F16 (1): FP16 (entries scaled by the power of two
+                              that brings the largest |entry| to at most 2^15, rounded to
+                              nearest; each row's FP32 sum scaled back): half the shared memory.
+                              KANN_PQ_LUT_U8 (2): uint8 values v = rint(clamp((entry - min_j) /
+                              scale, 0, 255)), min_j the minimum of subspace j, scale = (largest
+                              max_j - min_j) / 255, entries in FP32: a quarter of the shared
+                              memory (three queries per SM at m = 192).  Rows are ordered by the
+                              exact integer sum of their values; the distance reported (without
+                              re-rank) is sum_j min_j + scale * sum (two FP32 roundings). */
   uint32_t* d_status;      /* [n] per-query KANN_QSTAT_* bits, nullable */
   int32_t* d_counters;     /* [n][4] per-query counters, nullable: layer-0 distance
                               evaluations, layer-0 expansions, upper-layer distance

@@ -63,6 +63,7 @@ def lib():
             "orc_exact_sparse": [_p, _p, _p, _i64, _p, _p, _p, _i64, _i32, _i32, _p, _p],
             "orc_exact_pq": [_p, _p, _i64, _i32, _i32, _i32, _i32, _p, _i64, _i32, _p, _p],
             "orc_pq_lut": [_p, _i32, _i32, _i32, _i32, _i32, _p, _p],
+            "orc_pq_lut_u8": [_p, _i32, _i32, _i32, _i32, _p, _p, _p, _p],
             "orc_pq_encode": [_p, _i64, _i32, _i32, _i32, _p, _p],
             "orc_pq_reconstruct": [_p, _i64, _i32, _i32, _i32, _p, _p],
             "orc_pq_train": [_p, _i64, _i32, _i32, _i32, _i32, _u64, _p, _p],
@@ -228,10 +229,18 @@ def search_dense_multi(g, data, queries, k, ef, metric, expand, dtype=DT_F32, sc
     return ids, dists, cnt
 
 
-def search_pq(g, codes, codebooks, queries, k, ef, metric, form=FORM_FLAGS, nthreads=0, lut_f16=False):
-    """ADC search; lut_f16: the per-query table held in FP16 with a power-of-two
-    scale (each entry scaled so the largest |entry| is at most 2^15, rounded
-    to nearest, scaled back)."""
+LUT_EXACT, LUT_F16, LUT_U8 = 0, 1, 2
+
+
+def search_pq(g, codes, codebooks, queries, k, ef, metric, form=FORM_FLAGS, nthreads=0, lut_f16=False, lut=None):
+    """ADC search.  lut: LUT_EXACT (FP64 entries), LUT_F16 (the per-query table
+    held in FP16 with a power-of-two scale: each entry scaled so the largest
+    |entry| is at most 2^15, rounded to nearest, scaled back) or LUT_U8 (the
+    uint8 reading: FP32 entries quantised per query to 0..255 by
+    (entry - min_j) / scale; distances are the integer sums of those values,
+    see pq_lut_u8).  lut_f16=True is LUT_F16."""
+    if lut is None:
+        lut = LUT_F16 if lut_f16 else LUT_EXACT
     codes = _c(codes, np.uint8)
     codebooks = _c(codebooks, np.float32)
     queries = _c(queries, np.float32)
@@ -240,7 +249,7 @@ def search_pq(g, codes, codebooks, queries, k, ef, metric, form=FORM_FLAGS, nthr
     ids = np.empty((nq, k), np.int32)
     dists = np.empty((nq, k), np.float64)
     cnt = np.empty((nq, 4), np.int64)
-    lib().orc_search_pq(g.h, _ptr(codes), _ptr(codebooks), m, ksub, dsub, metric, int(bool(lut_f16)), _ptr(queries),
+    lib().orc_search_pq(g.h, _ptr(codes), _ptr(codebooks), m, ksub, dsub, metric, int(lut), _ptr(queries),
                         nq, k, ef, form, nthreads, _ptr(ids), _ptr(dists), _ptr(cnt))
     return ids, dists, cnt
 
@@ -346,6 +355,20 @@ def pq_reconstruct(codes, codebooks):
     out = np.empty((codes.shape[0], m * dsub), np.float32)
     lib().orc_pq_reconstruct(_ptr(codes), codes.shape[0], m, ksub, dsub, _ptr(codebooks), _ptr(out))
     return out
+
+
+def pq_lut_u8(codebooks, q, metric):
+    """The uint8 reading of one query's table: (values [m, 256] uint8, scale,
+    summin) -- a row's distance is summin + scale * (sum of its values), each
+    of the two operations rounded in FP32."""
+    codebooks = _c(codebooks, np.float32)
+    q = _c(q, np.float32)
+    m, ksub, dsub = codebooks.shape
+    v = np.empty((m, ksub), np.uint8)
+    sc = np.empty(1, np.float32)
+    sm = np.empty(1, np.float32)
+    lib().orc_pq_lut_u8(_ptr(codebooks), m, ksub, dsub, metric, _ptr(q), _ptr(v), _ptr(sc), _ptr(sm))
+    return v, sc[0], sm[0]
 
 
 def pq_lut(codebooks, q, metric, lut_f16=False):

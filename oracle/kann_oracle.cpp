@@ -230,18 +230,83 @@ struct DenseSpace : Space {
 // 2^e is the power of two that brings the largest |entry| to at most 2^15,
 // rounded to FP16 (nearest, ties to even), and scaled back; the scaling is
 // exact, so only the FP16 rounding of each entry remains.
+// lut mode 2, the uint8 reading (also a reading: the paper does not fix the
+// table's precision): every entry is computed in FP32 -- over the
+// sub-vector's dimensions in order, L2: u = q - c, s = fmaf(u, u, s); IP:
+// s = fmaf(q, c, s), entry -s -- then per subspace j min_j and range_j =
+// max_j - min_j (FP32), one scale = max_j range_j / 255 (FP32 division; 1
+// when every range is 0), and the entry's code value
+// v = rint(clamp((entry - min_j) / scale, 0, 255)) (FP32 subtraction and
+// division, ties to even; NaN counts as 0).  The row distance is the integer
+// sum of v over its codes -- exact, and ordered as (sum, id) -- and stands for
+// sum_j min_j + scale * sum.  Both the oracle and the kernel take these
+// FP32 decisions in the same operations, so the integer tables agree.
+struct PQTableU8 {
+  std::vector<uint8_t> v;  // [m][ksub]
+  float scale = 1.f, summin = 0.f;
+};
+
+PQTableU8 pq_table_u8(const float* codebooks, int m, int ksub, int dsub, int metric, const float* qv) {
+  PQTableU8 t;
+  std::vector<float> e((size_t)m * ksub), mn(m), mx(m);
+  for (int j = 0; j < m; ++j)
+    for (int c = 0; c < ksub; ++c) {
+      const float* C = codebooks + ((size_t)j * ksub + c) * dsub;
+      float s = 0.f;
+      for (int k = 0; k < dsub; ++k) {
+        const float q = qv[j * dsub + k], cc = C[k];
+        if (metric == MET_L2) {
+          const float u = q - cc;
+          s = std::fmaf(u, u, s);
+        } else {
+          s = std::fmaf(q, cc, s);
+        }
+      }
+      e[(size_t)j * ksub + c] = metric == MET_L2 ? s : -s;
+    }
+  float rmax = 0.f;
+  for (int j = 0; j < m; ++j) {
+    float lo = INFINITY, hi = -INFINITY;
+    for (int c = 0; c < ksub; ++c) {
+      lo = std::fmin(lo, e[(size_t)j * ksub + c]);
+      hi = std::fmax(hi, e[(size_t)j * ksub + c]);
+    }
+    mn[j] = lo;
+    mx[j] = hi;
+    rmax = std::fmax(rmax, hi - lo);
+  }
+  t.scale = rmax > 0.f ? rmax / 255.0f : 1.0f;
+  t.v.resize((size_t)m * ksub);
+  for (int j = 0; j < m; ++j)
+    for (int c = 0; c < ksub; ++c) {
+      const float r = std::fmin(std::fmax((e[(size_t)j * ksub + c] - mn[j]) / t.scale, 0.f), 255.f);
+      t.v[(size_t)j * ksub + c] = (uint8_t)std::rint(r);
+    }
+  float sm = 0.f;
+  for (int j = 0; j < m; ++j) sm += mn[j];
+  t.summin = sm;
+  return t;
+}
+
 struct PQSpace : Space {
   int m, ksub, dsub, metric;
   const uint8_t* codes;
   const float* codebooks;  // [m][ksub][dsub]
   std::vector<double> lut;
   bool lut_f16;
+  bool lut_u8;
 
-  PQSpace(const uint8_t* codes_, const float* cb_, int m_, int ksub_, int dsub_, int metric_, bool f16 = false)
+  // lut_mode: 0 exact (FP64 entries), 1 the FP16 reading, 2 the uint8 reading
+  PQSpace(const uint8_t* codes_, const float* cb_, int m_, int ksub_, int dsub_, int metric_, int lut_mode = 0)
       : m(m_), ksub(ksub_), dsub(dsub_), metric(metric_), codes(codes_), codebooks(cb_),
-        lut((size_t)m_ * ksub_), lut_f16(f16) {}
+        lut((size_t)m_ * ksub_), lut_f16(lut_mode == 1), lut_u8(lut_mode == 2) {}
 
   void set_query(const float* qv) {
+    if (lut_u8) {
+      const PQTableU8 t = pq_table_u8(codebooks, m, ksub, dsub, metric, qv);
+      for (size_t i = 0; i < lut.size(); ++i) lut[i] = t.v[i];
+      return;
+    }
     for (int j = 0; j < m; ++j)
       for (int c = 0; c < ksub; ++c) {
         const float* C = codebooks + ((size_t)j * ksub + c) * dsub;
@@ -801,12 +866,12 @@ void orc_search_dense_multi(const void* gp, int dtype, const void* data, const f
 }
 
 void orc_search_pq(const void* gp, const uint8_t* codes, const float* codebooks, int m, int ksub, int dsub,
-                   int metric, int lut_f16, const float* queries, int64_t nq, int k, int ef, int form,
+                   int metric, int lut_mode, const float* queries, int64_t nq, int k, int ef, int form,
                    int nthreads, int32_t* ids, double* dists, int64_t* counters) {
   const Graph& g = *(const Graph*)gp;
 #pragma omp parallel num_threads(threads_or_default(nthreads))
   {
-    PQSpace sp(codes, codebooks, m, ksub, dsub, metric, lut_f16 != 0);
+    PQSpace sp(codes, codebooks, m, ksub, dsub, metric, lut_mode);
 #pragma omp for schedule(dynamic, 1)
     for (int64_t qi = 0; qi < nq; ++qi) {
       sp.set_query(queries + (size_t)qi * m * dsub);
@@ -917,9 +982,19 @@ void orc_exact_pq(const uint8_t* codes, const float* codebooks, int64_t n, int m
 
 // ----------------------------- PQ ------------------------------------------
 // Per-query ADC table, [m][ksub] FP64.
-void orc_pq_lut(const float* codebooks, int m, int ksub, int dsub, int metric, int lut_f16, const float* q,
+// The uint8 reading of a query's table (values [m][ksub], scale, and the
+// FP32 sum of the per-subspace minima).
+void orc_pq_lut_u8(const float* codebooks, int m, int ksub, int dsub, int metric, const float* q, uint8_t* v,
+                   float* scale, float* summin) {
+  const PQTableU8 t = pq_table_u8(codebooks, m, ksub, dsub, metric, q);
+  std::copy(t.v.begin(), t.v.end(), v);
+  *scale = t.scale;
+  *summin = t.summin;
+}
+
+void orc_pq_lut(const float* codebooks, int m, int ksub, int dsub, int metric, int lut_mode, const float* q,
                 double* lut) {
-  PQSpace sp(nullptr, codebooks, m, ksub, dsub, metric, lut_f16 != 0);
+  PQSpace sp(nullptr, codebooks, m, ksub, dsub, metric, lut_mode);
   sp.set_query(q);
   std::memcpy(lut, sp.lut.data(), sizeof(double) * (size_t)m * ksub);
 }

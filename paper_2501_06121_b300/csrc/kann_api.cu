@@ -184,8 +184,8 @@ int fill_search_args(const kann_index_t* idx, const float* d_q, int n, int k, in
     a.lpr_override = l;
     if (opts->lean < -1 || opts->lean > 1) return KANN_EINVAL;
     a.lean = opts->lean > 0 ? 1 : 0;
-    if (opts->pq_lut_f16 < 0 || opts->pq_lut_f16 > 1) return KANN_EINVAL;
-    a.lut16 = opts->pq_lut_f16;
+    if (opts->pq_lut < KANN_PQ_LUT_F32 || opts->pq_lut > KANN_PQ_LUT_U8) return KANN_EINVAL;
+    a.lut = opts->pq_lut;
     if (opts->visited_format < 0 || opts->visited_format > 2) return KANN_EINVAL;
     vformat = opts->visited_format;
     if (opts->expand < 0 || opts->expand > KANN_MAX_EXPAND) return KANN_EINVAL;
@@ -217,7 +217,7 @@ int fill_search_args(const kann_index_t* idx, const float* d_q, int n, int k, in
 }
 
 // Shared-memory plan of a search with the settings in `a` (efcap, hbits,
-// lut16 filled in): bytes per warp (per team for PQ) and warps per CTA.  A
+// lut filled in): bytes per warp (per team for PQ) and warps per CTA.  A
 // PQ search drops visited-table bits (parity-safe: the table may forget)
 // until its query region fits one CTA.  Both the search and the admission
 // query (kann_search_workspace_bytes) take their answer from here.
@@ -226,10 +226,10 @@ int plan_shared(const kann_index_t* idx, SearchArgs& a, int& wpb) {
   if (idx->kind != 0 && a.expand > 1) return KANN_EINVAL;  // multi-expansion: dense indices
   if (idx->kind == 1) {
     const int m = idx->pq.m;
-    a.warp_smem = search_warp_smem_pq(a.efcap, a.hbits, a.vis_r >= 0, m, a.lut16 != 0);
+    a.warp_smem = search_warp_smem_pq(a.efcap, a.hbits, a.vis_r >= 0, m, a.lut);
     while (a.warp_smem + PQ_TEAM_CTL_BYTES > optin && a.hbits > 8) {
       set_visited(a, a.hbits - 1, a.vis_r >= 0);
-      a.warp_smem = search_warp_smem_pq(a.efcap, a.hbits, a.vis_r >= 0, m, a.lut16 != 0);
+      a.warp_smem = search_warp_smem_pq(a.efcap, a.hbits, a.vis_r >= 0, m, a.lut);
     }
     wpb = 1;  // one query per CTA (a team of warps sharing its table)
     return a.warp_smem + PQ_TEAM_CTL_BYTES > optin ? KANN_ENOMEM : KANN_OK;

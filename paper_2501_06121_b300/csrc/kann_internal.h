@@ -46,7 +46,7 @@ struct SearchArgs {
   int* work_counter;     // persistent mode: next query index (zeroed before launch), or null
   const int32_t* d_n;    // persistent mode: device-side query count (<= nq), or null
   int lean;              // dense: half the rows in flight, 64-register budget
-  int lut16;             // PQ: per-query table in FP16 with a power-of-two scale
+  int lut;               // PQ: per-query table format (KANN_PQ_LUT_F32 / F16 / U8)
   int efcap;       // W capacity (efmax rounded up to a multiple of 32)
   int expand;      // layer-0 entries expanded per step (1 = the HNSW step; 2..KANN_MAX_EXPAND: batched)
   int warp_smem;   // bytes of shared memory per warp
@@ -91,7 +91,7 @@ __host__ __device__ constexpr int cand_keys(int expand) { return 64 * expand + (
 // Per-warp shared memory needed by a dense search with these settings
 // (compact: a visited table of 16-bit slots, else 32-bit).
 int search_warp_smem(int efcap, int hbits, bool compact, int expand = 1);
-int search_warp_smem_pq(int efcap, int hbits, bool compact, int m, bool lut16 = false);
+int search_warp_smem_pq(int efcap, int hbits, bool compact, int m, int lut = KANN_PQ_LUT_F32);
 // Shared memory of a PQ search team's control block (after the query's region).
 constexpr int PQ_TEAM_CTL_BYTES = 64;
 int search_warp_smem_sparse(int efcap, int hbits, bool compact);

@@ -77,8 +77,10 @@ int launch_search_dense(const SearchArgs& a, int dtype, int wpb, void* stream) {
   return (int)cudaGetLastError();
 }
 
-int search_warp_smem_pq(int efcap, int hbits, bool compact, int m, bool lut16) {
-  return search_warp_smem(efcap, hbits, compact) + m * 256 * (lut16 ? 2 : 4);
+int search_warp_smem_pq(int efcap, int hbits, bool compact, int m, int lut) {
+  // uint8 table: the entries plus the subspace minima and ranges (8 m bytes)
+  const int table = lut == KANN_PQ_LUT_U8 ? m * 256 + 8 * m : m * 256 * (lut == KANN_PQ_LUT_F16 ? 2 : 4);
+  return search_warp_smem(efcap, hbits, compact) + table;
 }
 
 int search_warp_smem_sparse(int efcap, int hbits, bool compact) {
@@ -89,9 +91,19 @@ int launch_search_pq(const SearchArgs& a, int wpb, void* stream) {
   if (a.nq == 0) return 0;
   const int cplt = pow2_at_least((a.nchunks + a.lpr - 1) / a.lpr);
   SearchKernelFn fn = nullptr;
-  if (cplt == 1) fn = a.lut16 ? search_pq_kernel<1, true> : search_pq_kernel<1, false>;
-  if (cplt == 2) fn = a.lut16 ? search_pq_kernel<2, true> : search_pq_kernel<2, false>;
-  if (cplt == 4) fn = a.lut16 ? search_pq_kernel<4, true> : search_pq_kernel<4, false>;
+  static_assert(PQ_LUT_F16 == KANN_PQ_LUT_F16 && PQ_LUT_U8 == KANN_PQ_LUT_U8, "table formats");
+  switch (cplt * 4 + a.lut) {
+    case 4 + PQ_LUT_F32: fn = search_pq_kernel<1, PQ_LUT_F32>; break;
+    case 4 + PQ_LUT_F16: fn = search_pq_kernel<1, PQ_LUT_F16>; break;
+    case 4 + PQ_LUT_U8: fn = search_pq_kernel<1, PQ_LUT_U8>; break;
+    case 8 + PQ_LUT_F32: fn = search_pq_kernel<2, PQ_LUT_F32>; break;
+    case 8 + PQ_LUT_F16: fn = search_pq_kernel<2, PQ_LUT_F16>; break;
+    case 8 + PQ_LUT_U8: fn = search_pq_kernel<2, PQ_LUT_U8>; break;
+    case 16 + PQ_LUT_F32: fn = search_pq_kernel<4, PQ_LUT_F32>; break;
+    case 16 + PQ_LUT_F16: fn = search_pq_kernel<4, PQ_LUT_F16>; break;
+    case 16 + PQ_LUT_U8: fn = search_pq_kernel<4, PQ_LUT_U8>; break;
+    default: break;
+  }
   if (!fn) return (int)cudaErrorInvalidValue;
   (void)wpb;  // one query per CTA of PQ_TEAM warps
   static_assert(sizeof(TeamCtl) <= PQ_TEAM_CTL_BYTES, "team control block");

@@ -342,17 +342,28 @@ struct DenseBackend {
 // code bytes of an item; lanes own 16-byte chunks of it exactly as in the
 // dense back-end, summing their lookups in byte order.
 //
-// L16: the table is held in FP16 (half the shared memory, so twice the
-// queries per SM at m = 192): entries are scaled by 2^-e, with 2^e the power
-// of two that brings the largest |entry| to at most 2^15, rounded to nearest,
-// and the FP32 sum of a row's lookups is scaled back by 2^e (exact).
+// LF (table format) = PQ_LUT_F32, or
+//  PQ_LUT_F16: the table is held in FP16 (half the shared memory, so twice
+//   the queries per SM at m = 192): entries are scaled by 2^-e, with 2^e the
+//   power of two that brings the largest |entry| to at most 2^15, rounded to
+//   nearest, and the FP32 sum of a row's lookups is scaled back by 2^e;
+//  PQ_LUT_U8: a quarter of the shared memory: each FP32 entry becomes
+//   v = rint(clamp((entry - min_j) / scale, 0, 255)) with min_j the minimum
+//   of subspace j and scale = (largest range max_j - min_j) / 255; a row's
+//   distance is the integer sum of its values (exact, order-free), which
+//   stands for sum_j min_j + scale * sum (the output's distance).
 // ---------------------------------------------------------------------------
-template <int CPL, bool L16>
+constexpr int PQ_LUT_F32 = 0, PQ_LUT_F16 = 1, PQ_LUT_U8 = 2;
+
+template <int CPL, int LF>
 struct PQBackend {
+  static constexpr bool L16 = LF == PQ_LUT_F16;
+  static constexpr bool U8 = LF == PQ_LUT_U8;
   static constexpr int U = (8 / CPL) > 0 ? (8 / CPL) : 1;
-  typedef typename std::conditional<L16, __half, float>::type LutT;
+  typedef typename std::conditional<U8, uint8_t, typename std::conditional<L16, __half, float>::type>::type LutT;
   LutT* lut;
-  float scale;  // 2^e for the FP16 table, 1 otherwise
+  float scale;   // 2^e for the FP16 table, the step of the uint8 table, 1 otherwise
+  float summin;  // uint8 table: sum of the subspace minima (FP32, in subspace order)
 
   __device__ __forceinline__ static float entry(const SearchArgs& a, const float* q, int e) {
     const int j = e >> 8, dsub = a.pq_dsub;
@@ -372,6 +383,7 @@ struct PQBackend {
   }
 
   __device__ __forceinline__ void init(const SearchArgs& a, int qi, int lane, unsigned char* extra) {
+    static_assert(!U8, "the uint8 table is built by a team");
     lut = reinterpret_cast<LutT*>(extra);
     const int m = a.pq_m;
     const float* q = a.q + (size_t)qi * m * a.pq_dsub;
@@ -400,6 +412,45 @@ struct PQBackend {
     const float* q = a.q + (size_t)qi * m * a.pq_dsub;
     const int t0 = w * 32 + lane, step = T * 32;
     scale = 1.f;
+    summin = 0.f;
+    if constexpr (U8) {
+      // per-subspace minima and ranges (warp w takes subspaces w, w + T, ...),
+      // kept after the table
+      float* mn = reinterpret_cast<float*>(s.extra + (size_t)m * 256);
+      float* rg = mn + m;
+      for (int j = w; j < m; j += T) {
+        float lo = __int_as_float(0x7f800000), hi = __int_as_float(0xff800000);
+        for (int c = lane; c < 256; c += 32) {
+          const float e = entry(a, q, j * 256 + c);
+          lo = fminf(lo, e);
+          hi = fmaxf(hi, e);
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          lo = fminf(lo, __shfl_xor_sync(FULL, lo, o));
+          hi = fmaxf(hi, __shfl_xor_sync(FULL, hi, o));
+        }
+        if (lane == 0) {
+          mn[j] = lo;
+          rg[j] = __fsub_rn(hi, lo);
+        }
+      }
+      team_bar(T);
+      float rmax = 0.f;
+      for (int j = lane; j < m; j += 32) rmax = fmaxf(rmax, rg[j]);
+      for (int o = 16; o > 0; o >>= 1) rmax = fmaxf(rmax, __shfl_xor_sync(FULL, rmax, o));
+      scale = rmax > 0.f ? __fdiv_rn(rmax, 255.0f) : 1.0f;
+      for (int e = t0; e < m * 256; e += step) {
+        const float r = fminf(fmaxf(__fdiv_rn(__fsub_rn(entry(a, q, e), mn[e >> 8]), scale), 0.f), 255.f);
+        lut[e] = (uint8_t)__float2uint_rn(r);
+      }
+      if (w == 0) {
+        float sm = 0.f;
+        for (int j = 0; j < m; ++j) sm = __fadd_rn(sm, mn[j]);
+        summin = sm;
+      }
+      team_bar(T);
+      return;
+    }
     if (!L16) {
       for (int e = t0; e < m * 256; e += step) lut[e] = entry(a, q, e);
     } else {
@@ -417,6 +468,12 @@ struct PQBackend {
       scale = ldexpf(1.f, sh);
     }
     team_bar(T);
+  }
+
+  // the distance the output reports for a traversal key's value
+  __device__ __forceinline__ float out_dist(float d) const {
+    if constexpr (U8) return __fadd_rn(__fmul_rn(scale, d), summin);
+    return d;
   }
 
   __device__ __forceinline__ void dists(const SearchArgs& a, const int* cid, int cnt, u64* ck, int lane) {
@@ -440,6 +497,7 @@ struct PQBackend {
         if (base + u * rpi >= cnt) break;  // this and later row groups are empty
         const int r = base + u * rpi + grp;
         float acc = 0.f;
+        uint32_t iacc = 0u;  // uint8 table: exact integer sum (at most 512 * 255)
 #pragma unroll
         for (int c = 0; c < CPL; ++c) {
           const int ch = sub + c * lpr;
@@ -449,12 +507,18 @@ struct PQBackend {
 #pragma unroll
             for (int b = 0; b < 16; ++b) {
               const LutT v = L[b * 256 + ((w[b >> 2] >> (8 * (b & 3))) & 0xffu)];
-              if constexpr (L16) acc += __half2float(v);
+              if constexpr (U8) iacc += v;
+              else if constexpr (L16) acc += __half2float(v);
               else acc += v;
             }
           }
         }
-        for (int o = lpr >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
+        if constexpr (U8) {
+          for (int o = lpr >> 1; o > 0; o >>= 1) iacc += __shfl_xor_sync(FULL, iacc, o);
+          acc = (float)iacc;
+        } else {
+          for (int o = lpr >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
+        }
         if (L16) acc *= scale;
         if (sub == 0 && r < cnt) ck[r] = make_key(acc, (uint32_t)cid[r]);
       }
@@ -799,6 +863,13 @@ __device__ __forceinline__ void merge_batch(u64 e0, u64 e1, u64* W, int& len, in
 
 template <class B>
 __device__ __forceinline__ uint32_t backend_status(const B&) { return 0u; }
+
+// The distance the output reports for a traversal key (the PQ back-end's
+// uint8 table keeps integer sums in W); identity for the others.
+template <class B>
+__device__ __forceinline__ float backend_out_dist(const B&, float d) { return d; }
+template <int CPL, int LF>
+__device__ __forceinline__ float backend_out_dist(const PQBackend<CPL, LF>& b, float d) { return b.out_dist(d); }
 __device__ __forceinline__ uint32_t backend_status(const SparseBackend& b) {
   return b.trunc ? KANN_QSTAT_QUERY_TRUNCATED : 0u;
 }
@@ -1094,7 +1165,8 @@ __device__ __forceinline__ void search_one(const SearchArgs& a, B& be, int qi, i
 
   // 4. exact re-rank of the best R entries
   int nout = len;
-  if (a.R != 0 && a.rr_data != nullptr) {
+  const bool reranked = a.R != 0 && a.rr_data != nullptr;
+  if (reranked) {
     const int R = min(a.R < 0 ? ef : a.R, len);
     nout = rerank_phase(a.rr_data, a.rr_dtype, a.rr_stride, a.rr_nchunks, a.rr_lpr, a.metric, a.q + (size_t)qi * a.d, R, W, ck,
                         cid, lane, tc, T);
@@ -1109,6 +1181,7 @@ __device__ __forceinline__ void search_one(const SearchArgs& a, B& be, int qi, i
       const u64 key = kmask(W[j]);
       id = (int32_t)key_id(key);
       dd = key_dist(key);
+      if (!reranked) dd = backend_out_dist(be, dd);
     }
     a.out_ids[(size_t)qi * ld + j] = id;
     a.out_d[(size_t)qi * ld + j] = dd;
@@ -1227,9 +1300,16 @@ __global__ void __launch_bounds__(128, MinBlocks<DT, CPLT, LEAN>::value) search_
 
 constexpr int PQ_TEAM = 8;  // warps sharing one query's lookup table (TeamCtl::wmax holds 8)
 
-template <int CPLT, bool L16>
-__global__ void __launch_bounds__(PQ_TEAM * 32, 1) search_pq_kernel(const SearchArgs a) {
-  PQBackend<CPLT, L16> be;
+// Teams per SM the kernel is compiled for: the uint8 table (48 KB at m = 192)
+// lets three 8-warp teams share an SM (80 registers a thread).
+template <int LF>
+struct PQTeamsPerSM {
+  static constexpr int value = LF == PQ_LUT_U8 ? 3 : 1;
+};
+
+template <int CPLT, int LF>
+__global__ void __launch_bounds__(PQ_TEAM * 32, PQTeamsPerSM<LF>::value) search_pq_kernel(const SearchArgs a) {
+  PQBackend<CPLT, LF> be;
   run_queries_team<PQ_TEAM>(a, be);
 }
 

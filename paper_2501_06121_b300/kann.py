@@ -61,7 +61,7 @@ class kann_sparse_desc(ctypes.Structure):
 class kann_search_opts(ctypes.Structure):
     _fields_ = [("rerank", ctypes.c_int32), ("max_hops", ctypes.c_int32), ("hash_bits", ctypes.c_int32),
                 ("warps_per_block", ctypes.c_int32), ("lanes_per_row", ctypes.c_int32), ("lean", ctypes.c_int32),
-                ("pq_lut_f16", ctypes.c_int32),
+                ("pq_lut", ctypes.c_int32),
                 ("d_status", ctypes.c_void_p), ("d_counters", ctypes.c_void_p),
                 ("d_work_counter", ctypes.c_void_p), ("d_n", ctypes.c_void_p),
                 ("visited_format", ctypes.c_int32), ("expand", ctypes.c_int32)]
@@ -209,14 +209,17 @@ def kann_index_upload(graph, vectors=None, dtype=KANN_F32, metric=KANN_L2, scale
 
 
 KANN_VISITED_AUTO, KANN_VISITED_COMPACT, KANN_VISITED_WIDE = 0, 1, 2
+KANN_PQ_LUT_F32, KANN_PQ_LUT_F16, KANN_PQ_LUT_U8 = 0, 1, 2
 
 
 def _opts(rerank=0, max_hops=0, hash_bits=0, warps_per_block=0, lanes_per_row=0, status=None, counters=None,
-          work_counter=None, n_device=None, lean=0, pq_lut_f16=0, visited_format=0, expand=0):
+          work_counter=None, n_device=None, lean=0, pq_lut_f16=0, visited_format=0, expand=0, pq_lut=None):
     _require_cuda(status, counters, work_counter, n_device)
     p = lambda t: t.data_ptr() if t is not None else None
+    if pq_lut is None:  # pq_lut_f16=1 is the FP16 table
+        pq_lut = KANN_PQ_LUT_F16 if pq_lut_f16 else KANN_PQ_LUT_F32
     return kann_search_opts(int(rerank), int(max_hops), int(hash_bits), int(warps_per_block), int(lanes_per_row),
-                            int(lean), int(pq_lut_f16),
+                            int(lean), int(pq_lut),
                             p(status), p(counters), p(work_counter), p(n_device), int(visited_format),
                             int(expand))
 
@@ -227,7 +230,8 @@ def kann_search(index, queries, k, ef, ids=None, dists=None, stream=None):
 
 def kann_search_ex(index, queries, k, ef, ids=None, dists=None, stream=None, **opts):
     """queries [n, d] float32 on the device -> (ids [n, k] int32, dists [n, k] float32).
-    opts: rerank, max_hops, hash_bits, warps_per_block, lanes_per_row, lean, pq_lut_f16 (PQ: FP16 table),
+    opts: rerank, max_hops, hash_bits, visited_format, expand, warps_per_block, lanes_per_row, lean,
+    pq_lut (PQ table format: KANN_PQ_LUT_F32 / F16 / U8; pq_lut_f16=1 is the FP16 table),
     work_counter ([1] int32
     tensor: persistent work-stealing launch), n_device ([1] int32: device-side query count,
     persistent mode), status ([n] int32

@@ -92,6 +92,33 @@ def test_pq_m192_parity(set768, ef, lut_f16):
     check_adc(cb, codes, Q, gi, gd, O.IP, lut_f16)
 
 
+@pytest.mark.parametrize("ef", [128, 1000])
+def test_pq_m192_u8_table_bit_exact(set768, ef):
+    # the uint8 table at m = 192 (48 KB, three teams per SM): identical
+    # integer decisions on both sides
+    X, Q, g, cb, codes = set768
+    idx = pq_index(g, cb, codes, K.KANN_IP)
+    oi, od, oc = O.search_pq(g, codes, cb, Q, 10, ef, O.IP, lut=O.LUT_U8)
+    cnt = torch.zeros((len(Q), 4), dtype=torch.int32, device="cuda")
+    gi, gd = K.kann_search_ex(idx, dev(Q), 10, ef, pq_lut=K.KANN_PQ_LUT_U8, counters=cnt, hash_bits=14)
+    torch.cuda.synchronize()
+    assert np.array_equal(gi.cpu().numpy(), oi)
+    assert np.array_equal(cnt.cpu().numpy().astype(np.int64), oc)
+
+
+@pytest.mark.parametrize("k", [10, 100])
+def test_pq_m192_u8_table_rerank100(set768, k):
+    X, Q, g, cb, codes = set768
+    idx = pq_index(g, cb, codes, K.KANN_IP, rerank=dev(X))
+    ti, _, _ = O.search_pq(g, codes, cb, Q, 128, 128, O.IP, lut=O.LUT_U8)
+    oi, od = O.rerank_dense(X, Q, ti[:, :100], k, O.IP)
+    gi, gd = K.kann_search_ex(idx, dev(Q), k, 128, rerank=100, pq_lut=K.KANN_PQ_LUT_U8)
+    torch.cuda.synchronize()
+    gi, gd = gi.cpu().numpy(), gd.cpu().numpy()
+    assert id_set_match_fraction(gi, oi) >= 0.999
+    check_ip(X, Q, gi, gd)
+
+
 def test_pq_m192_l2_parity(set768):
     X, Q, g, cb, codes = set768
     idx = pq_index(g, cb, codes, K.KANN_L2)
@@ -119,16 +146,18 @@ def test_pq_m192_rerank100_on_fp32_rows(set768, k, lut_f16):
     check_ip(X, Q, gi, gd)
 
 
-def test_pq_m192_ef1024_shrinks_the_visited_table_and_keeps_parity(set768):
-    # FP32 table 192 KB + beam 8 KB + candidates 1 KB + the default 2^13-slot
-    # table 32 KB exceed one CTA: the search runs with fewer table bits, which
-    # only makes it forget visited ids (parity-safe)
+@pytest.mark.parametrize("fmt,hb", [(K.KANN_VISITED_WIDE, 0), (K.KANN_VISITED_COMPACT, 16)])
+def test_pq_m192_ef1024_shrinks_the_visited_table_and_keeps_parity(set768, fmt, hb):
+    # FP32 table 192 KB + beam 8 KB + candidates + a visited table of 2^13
+    # wide (32 KB) or 2^16 compact (128 KB) slots exceed one CTA: the search
+    # runs with fewer table bits, which only makes it forget visited ids
+    # (parity-safe)
     X, Q, g, cb, codes = set768
     idx = pq_index(g, cb, codes, K.KANN_IP)
-    assert K.kann_search_workspace_bytes(idx, len(Q), 10, 1024) > 0
+    assert K.kann_search_workspace_bytes(idx, len(Q), 10, 1024, visited_format=fmt, hash_bits=hb) > 0
     st = torch.zeros(len(Q), dtype=torch.int32, device="cuda")
     oi, od, _ = O.search_pq(g, codes, cb, Q, 10, 1024, O.IP)
-    gi, gd = K.kann_search_ex(idx, dev(Q), 10, 1024, status=st)
+    gi, gd = K.kann_search_ex(idx, dev(Q), 10, 1024, status=st, visited_format=fmt, hash_bits=hb)
     torch.cuda.synchronize()
     gi, gd = gi.cpu().numpy(), gd.cpu().numpy()
     assert id_set_match_fraction(gi, oi) >= 0.999
@@ -205,11 +234,11 @@ def test_workspace_bytes_is_positive_exactly_when_the_search_runs():
         codes = rng.integers(0, 256, (n, m)).astype(np.uint8)
         idx = pq_index(g, cb, codes, K.KANN_L2)
         seen = set()
-        for lut16 in (0, 1):
+        for lut in (K.KANN_PQ_LUT_F32, K.KANN_PQ_LUT_F16, K.KANN_PQ_LUT_U8):
             for efmax in (16, 64, 256, 512, 1024, 1025):
-                ws = K.kann_search_workspace_bytes(idx, 8, 10, efmax, pq_lut_f16=lut16)
-                ran = _runs(lambda: K.kann_search_ex(idx, Q, 10, efmax, pq_lut_f16=lut16))
-                assert (ws > 0) == ran, (m, lut16, efmax, ws)
+                ws = K.kann_search_workspace_bytes(idx, 8, 10, efmax, pq_lut=lut)
+                ran = _runs(lambda: K.kann_search_ex(idx, Q, 10, efmax, pq_lut=lut))
+                assert (ws > 0) == ran, (m, lut, efmax, ws)
                 seen.add(ran)
         if m == 384:
             assert seen == {True, False}

@@ -206,3 +206,26 @@ def test_sparse_exact_knn_matches_oracle():
     mag = np.einsum("qd,qkd->qk", np.abs(Qd), np.abs(Xd[gi]))
     assert np.all(np.abs(gd - ref) <= 1e-5 * np.maximum(np.abs(ref), mag) + 1e-30)
     assert np.all(np.diff(gd, axis=1) >= 0)
+
+
+@pytest.mark.parametrize("metric", [K.KANN_IP, K.KANN_L2])
+def test_pq_u8_table_bit_exact(pq_setup, metric):
+    # the uint8 table: both sides build it with the same FP32 operations and
+    # order rows by exact integer sums, so ids, work and the reported
+    # distances (summin + scale * sum, two FP32 roundings) are identical
+    X, Q, g, cb, codes = pq_setup
+    idx = K.kann_index_upload(K.graph_to_device(g.arrays()),
+                              pq=dict(codes=dev(codes), codebooks=dev(cb), metric=metric))
+    for ef in (16, 64, 200):
+        oi, od, oc = O.search_pq(g, codes, cb, Q, 10, ef, metric, lut=O.LUT_U8)
+        cnt = torch.zeros((len(Q), 4), dtype=torch.int32, device="cuda")
+        gi, gd = K.kann_search_ex(idx, dev(Q), 10, ef, pq_lut=K.KANN_PQ_LUT_U8, counters=cnt, hash_bits=15)
+        torch.cuda.synchronize()
+        gi, gd = gi.cpu().numpy(), gd.cpu().numpy()
+        assert np.array_equal(gi, oi), ef
+        assert np.array_equal(cnt.cpu().numpy().astype(np.int64), oc), ef
+        want = np.empty(gd.shape, np.float32)
+        for qi in range(len(Q)):
+            _, sc, sm = O.pq_lut_u8(cb, Q[qi], metric)
+            want[qi] = np.float32(sm) + np.float32(sc) * od[qi].astype(np.float32)
+        assert np.array_equal(gd, want), ef

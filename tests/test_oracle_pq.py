@@ -2,6 +2,7 @@
 kANNolo Sec. 2): ADC identities, the exact special case, k-means descent,
 nearest-centroid encoding."""
 import numpy as np
+import pytest
 
 import oracle as O
 
@@ -110,3 +111,79 @@ def test_fp16_table_is_exact_on_small_integer_tables():
         a = O.search_pq(g, codes, cb, Q, 10, 40, metric, lut_f16=True)
         b = O.search_pq(g, codes, cb, Q, 10, 40, metric)
         assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
+# ------------------------------------------------------------------ the uint8 table reading
+def _numpy_u8_table(cb, q, metric):
+    """The uint8 reading written out with numpy float32 for dsub = 1 (each
+    entry is then one correctly rounded FP32 product, as fmaf gives it)."""
+    m, ksub, dsub = cb.shape
+    assert dsub == 1
+    c = cb[:, :, 0].astype(np.float32)
+    qq = q.astype(np.float32).reshape(m, 1)
+    if metric == O.L2:
+        u = qq - c
+        e = u * u
+    else:
+        e = -(qq * c)
+    mn = e.min(1)
+    rng = e.max(1) - mn
+    rmax = np.float32(rng.max())
+    scale = np.float32(rmax / np.float32(255.0)) if rmax > 0 else np.float32(1.0)
+    r = np.clip((e - mn[:, None]) / scale, np.float32(0), np.float32(255))
+    v = np.rint(r).astype(np.uint8)
+    summin = np.float32(0)
+    for x in mn:
+        summin = np.float32(summin + x)
+    return v, scale, summin
+
+
+@pytest.mark.parametrize("metric", [O.L2, O.IP])
+def test_u8_table_equals_its_definition_written_in_numpy(metric):
+    rng = np.random.default_rng(17)
+    cb = (rng.standard_normal((32, 256, 1)) * 3).astype(np.float32)
+    for _ in range(5):
+        q = rng.standard_normal(32).astype(np.float32) * 2
+        v, sc, sm = O.pq_lut_u8(cb, q, metric)
+        nv, nsc, nsm = _numpy_u8_table(cb, q, metric)
+        assert np.array_equal(v, nv) and sc == nsc and sm == nsm
+        assert v.min(1).max() == 0 and v.max() == 255  # each subspace's minimum -> 0, the widest reaches 255
+
+
+def test_u8_table_is_exact_on_integer_entries_spanning_255():
+    # IP with q = 1 and codebook values -255..0 (both ends present in every
+    # subspace): entries are the integers 0..255, so scale = 1, the minima are
+    # 0 and the uint8 search is the exact ADC search
+    rng = np.random.default_rng(19)
+    m = 16
+    cb = -rng.integers(0, 256, (m, 256, 1)).astype(np.float32)
+    cb[:, 0, 0], cb[:, 1, 0] = 0.0, -255.0
+    X = rng.standard_normal((2500, m)).astype(np.float32)
+    codes = rng.integers(0, 256, (2500, m)).astype(np.uint8)
+    Q = np.ones((40, m), np.float32)
+    v, sc, sm = O.pq_lut_u8(cb, Q[0], O.IP)
+    assert sc == 1.0 and sm == 0.0
+    g = O.build_dense(X, O.L2, 10, 50, 19)
+    a = O.search_pq(g, codes, cb, Q, 10, 64, O.IP)
+    b = O.search_pq(g, codes, cb, Q, 10, 64, O.IP, lut=O.LUT_U8)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1]) and np.array_equal(a[2], b[2])
+
+
+@pytest.mark.parametrize("metric", [O.L2, O.IP])
+def test_u8_distance_within_half_a_step_per_subspace(metric):
+    # summin + scale * sum differs from the exact ADC distance by at most
+    # m * scale / 2 (each value rounds to the nearest step) plus the FP32
+    # rounding of the entries
+    rng = np.random.default_rng(23)
+    m, dsub = 24, 4
+    cb = rng.standard_normal((m, 256, dsub)).astype(np.float32)
+    codes = rng.integers(0, 256, (500, m)).astype(np.uint8)
+    for _ in range(5):
+        q = rng.standard_normal(m * dsub).astype(np.float32)
+        v, sc, sm = O.pq_lut_u8(cb, q, metric)
+        exact = O.pq_lut(cb, q, metric)
+        S = v[np.arange(m)[None, :], codes].astype(np.float64).sum(1)
+        approx = np.float64(sm) + np.float64(sc) * S
+        ref = exact[np.arange(m)[None, :], codes].sum(1)
+        mag = np.abs(exact[np.arange(m)[None, :], codes]).sum(1)
+        assert np.all(np.abs(approx - ref) <= m * sc / 2 * (1 + 1e-5) + 1e-5 * mag)

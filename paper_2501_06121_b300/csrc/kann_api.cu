@@ -208,8 +208,12 @@ int fill_search_args(const kann_index_t* idx, const float* d_q, int n, int k, in
     // distances to an FP32 traversal when the copy is FP32)
     a.rr_lpr = lanes_per_row(a.rr_nchunks, default_chunks_per_lane(idx->rr.dtype));
   }
-  // visited table: compact unless asked for wide (or the ids do not fit it)
-  const bool compact_ok = set_visited(a, hbits ? hbits : default_hbits(a.efmax, true), true);
+  // visited table: compact unless asked for wide (or the ids do not fit it);
+  // a PQ search with the uint8 table takes 2,048 slots so that four teams
+  // fit an SM at m = 192
+  int hb_compact = default_hbits(a.efmax, true);
+  if (idx->kind == 1 && a.lut == KANN_PQ_LUT_U8) hb_compact = 11;
+  const bool compact_ok = set_visited(a, hbits ? hbits : hb_compact, true);
   if (vformat == 1 && !compact_ok) return KANN_EINVAL;
   if (vformat == 2 || !compact_ok) set_visited(a, hbits ? hbits : default_hbits(a.efmax, false), false);
   a.efcap = (a.efmax + 31) / 32 * 32;  // beam capacity: efmax rounded up to whole warp rows

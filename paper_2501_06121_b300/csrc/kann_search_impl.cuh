@@ -1301,10 +1301,12 @@ __global__ void __launch_bounds__(128, MinBlocks<DT, CPLT, LEAN>::value) search_
 constexpr int PQ_TEAM = 8;  // warps sharing one query's lookup table (TeamCtl::wmax holds 8)
 
 // Teams per SM the kernel is compiled for: the uint8 table (48 KB at m = 192)
-// lets three 8-warp teams share an SM (80 registers a thread).
+// lets four 8-warp teams share an SM (64 registers a thread; measured 11%
+// faster than three teams at 80 registers on a 200k x 768 set, despite the
+// spills).
 template <int LF>
 struct PQTeamsPerSM {
-  static constexpr int value = LF == PQ_LUT_U8 ? 3 : 1;
+  static constexpr int value = LF == PQ_LUT_U8 ? 4 : 1;
 };
 
 template <int CPLT, int LF>

@@ -741,6 +741,29 @@ def main():
                           "qps": N_QUERY / (ms_m / 1e3), "ms": ms_m,
                           "vs_one_expansion_qps": N_QUERY / (ms_m / 1e3) / qps})
 
+    # the same graph built with the layer-0 insertions on the GPU: build time
+    # and the headline form's recall at the selected ef on it
+    build_dev = None
+    if rank == 0 and not args.no_curve:
+        torch.cuda.synchronize()
+        t_b = time.time()
+        g_dev = K_.kann_hnsw_build_device(Xd, K_.KANN_L2, M, EFC, SEED)
+        t_b = time.time() - t_b
+        idx_dev = K_.kann_index_upload(K_.graph_to_device(g_dev, dev), vectors=Xh, dtype=K_.KANN_F16, metric=K_.KANN_L2,
+                                       rerank=Xd)
+        rec_dev = {}
+        for e in sorted(set([ef] + [x for x in EF_SWEEP if x <= 128])):
+            ids_g, _ = K_.kann_search_ex(idx_dev, Qd, K, e, rerank=-1)
+            ids_h, _ = K_.kann_search_ex(idx16, Qd, K, e, rerank=-1)
+            torch.cuda.synchronize()
+            rec_dev[str(e)] = {"device_graph": recall_at(ids_g.cpu().numpy(), gt),
+                               "host_graph": recall_at(ids_h.cpu().numpy(), gt)}
+        build_dev = {"device_build_s": t_b, "host_build_s": build_s if not cached else None,
+                     "host_build_cached": cached, "recall@10_fp16_rerank": rec_dev,
+                     "rule": "kann_hnsw_build_device: upper-layer nodes on the host, level-0 nodes on the GPU in "
+                             "batches of 1/32 of the graph; same M, efConstruction and levels"}
+        del idx_dev, g_dev
+
     serving = None
     if rank == 0 and world == 1 and not args.no_serving:
         serving = run_serving(g, Xd, Q, dev, args)
@@ -785,6 +808,7 @@ def main():
             "serving": serving,
             "recall_qps_curve": curve,
             "multi_expansion": multi,
+            "graph_build_device": build_dev,
         }
         print(json.dumps(out))
     if world > 1:

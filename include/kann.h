@@ -359,6 +359,31 @@ int kann_hnsw_build_sparse(const int64_t* h_indptr, const uint16_t* h_terms, con
                            int M, int ef_construction, uint64_t seed, int nthreads, const int8_t* h_level,
                            int32_t* h_l0, int32_t* h_upper_slot, int32_t* h_upper, int32_t* h_entry);
 
+/* ---- graph construction (layer 0 on the device) ---------------------------
+ * The same HNSW (Malkov & Yashunin Alg. 1 with the Alg. 4 heuristic, caps M
+ * and 2M, levels from kann_hnsw_levels) with the layer-0 insertions on the
+ * GPU.  The nodes of level >= 1 (about n / M) are inserted first, on the host
+ * with `nthreads` threads (all their layers); the level-0 nodes follow in id
+ * order, in batches of at most 1/32 of the nodes already inserted (and
+ * at most `batch`, 0 = 65,536): each batch node's efConstruction best
+ * candidates come from the library's search on the graph so far, it keeps up
+ * to M of them by the heuristic, and each kept neighbour appends the node to
+ * its list or, past 2M, shrinks its list with the same heuristic.  Nodes of
+ * one batch do not link to each other, and a node takes at most 16 reverse
+ * links per batch (the others keep their forward edge only).  Distances are
+ * FP32.  d_x [n][d] FP32 device rows (16-byte aligned, d a multiple of 4);
+ * h_level [n] host levels; outputs are caller-owned device arrays sized as
+ * for kann_hnsw_build_dense: d_l0 [n][2M], d_upper_slot [n], d_upper
+ * [n_upper][max_level][M] (may be NULL when max_level == 0); *h_entry
+ * receives the entry point.  d_ws is device scratch of
+ * kann_hnsw_build_device_workspace_bytes(n, d, M, ef_construction, batch)
+ * bytes.  Synchronises `stream` (the host part needs the upper nodes' rows).
+ * Errors: KANN_EINVAL, KANN_ECUDA. */
+size_t kann_hnsw_build_device_workspace_bytes(int64_t n, int d, int M, int ef_construction, int batch);
+int kann_hnsw_build_device(const float* d_x, int64_t n, int d, int metric, int M, int ef_construction, uint64_t seed,
+                           int batch, int nthreads, const int8_t* h_level, int32_t* d_l0, int32_t* d_upper_slot,
+                           int32_t* d_upper, int32_t* h_entry, void* d_ws, size_t ws_bytes, void* stream);
+
 /* ---- diagnostics --------------------------------------------------------*/
 const char* kann_status_str(int status);
 /* The cudaError_t of the most recent failed CUDA call in this thread. */

@@ -97,6 +97,8 @@ def _lib():
             "kann_pq_train_workspace_bytes": (SZ, [I, I]),
             "kann_pq_train": (I, [P, I64, I, I, I, U64, P, P, SZ, P]),
             "kann_pq_encode": (I, [P, I64, I, I, P, P, P]),
+            "kann_hnsw_build_device_workspace_bytes": (SZ, [I64, I, I, I, I]),
+            "kann_hnsw_build_device": (I, [P, I64, I, I, I, I, U64, I, I, P, P, P, P, P, P, SZ, P]),
             "kann_status_str": (ctypes.c_char_p, [I]),
             "kann_last_cuda_error": (I, []),
         }
@@ -430,6 +432,33 @@ def kann_hnsw_build_sparse(csr, M, ef_construction, seed, nthreads=0):
                                                                    ef_construction, seed, nthreads, _vp(level),
                                                                    _vp(l0), _vp(us), _vp(up), ctypes.byref(entry)))
     return dict(n=n, M=M, M0=2 * M, max_level=L, entry=entry.value, level=level, l0=l0, upper_slot=us, upper=up)
+
+
+def kann_hnsw_build_device(x, metric, M, ef_construction, seed, batch=0, nthreads=0, stream=None):
+    """HNSW over FP32 device rows x [n, d] with the layer-0 insertions on the
+    GPU (the upper-layer nodes are inserted on the host first).  Returns the
+    serialised graph as a dict of numpy arrays (as kann_hnsw_build_dense)."""
+    _require_cuda(x)
+    if x.dtype != torch.float32 or x.dim() != 2:
+        raise ValueError("kann_hnsw_build_device: x must be [n, d] float32")
+    n, d = x.shape
+    level, L, nu, l0, us, up = _graph_buffers(n, M, seed)
+    dev = x.device
+    with torch.cuda.device(dev):
+        d_l0 = torch.empty((n, 2 * M), dtype=torch.int32, device=dev)
+        d_us = torch.empty(n, dtype=torch.int32, device=dev)
+        d_up = torch.empty(up.shape, dtype=torch.int32, device=dev)
+        wsb = int(_lib().kann_hnsw_build_device_workspace_bytes(n, d, M, ef_construction, batch))
+        ws = torch.empty(max(wsb, 16), dtype=torch.uint8, device=dev)
+        entry = ctypes.c_int32()
+        _check("kann_hnsw_build_device", _lib().kann_hnsw_build_device(
+            _dev(x), n, d, metric, M, ef_construction, seed, batch, nthreads, _vp(level), _dev(d_l0), _dev(d_us),
+            _dev(d_up), ctypes.byref(entry), _dev(ws), ws.numel(), _stream(stream)))
+        torch.cuda.synchronize()
+    if L > 0:
+        up = d_up.cpu().numpy()
+    return dict(n=n, M=M, M0=2 * M, max_level=L, entry=entry.value, level=level, l0=d_l0.cpu().numpy(),
+                upper_slot=d_us.cpu().numpy(), upper=up)
 
 
 KANN_NOALLOC_SCRATCH_BYTES = 16 << 20

@@ -434,27 +434,33 @@ def run_pq768(args, n=None, concentration=None):
     print(json.dumps(out))
 
 
-def run_sparse(args, n_docs=100_000):
-    """The Splade-shaped workload at reduced size: 100k documents over a
+def run_sparse(args, n_docs=None):
+    """The Splade-shaped workload: `--sparse-n` documents (default 1M) over a
     30,522-term vocabulary (nnz ~ Poisson(120), Zipf(1.1) terms, lognormal
     weights), 10k queries (nnz ~ Poisson(40)), inner product, HNSW M=32
-    efC=200 built on the host; QPS over all queries, recall@10 against the
-    GPU sparse brute force on the first 1,000 queries."""
+    efC=200 built with the layer-0 insertions on the GPU (`--sparse-host-build`:
+    the host builder); QPS over all queries, recall@10 against the GPU sparse
+    brute force on the first 1,000 queries, and the roofline of the search
+    kernel on its algorithmic bytes."""
     import torch
     from paper_2501_06121_b300 import build as lib_build
     from paper_2501_06121_b300 import datagen as G
     from paper_2501_06121_b300 import kann as K_
     lib_build.build()
     dev = torch.device("cuda", 0)
+    n_docs = n_docs or args.sparse_n
     t0 = time.time()
     base, qs = G.sparse_zipf(n_docs, 10_000, vocab=30522, lam_doc=120, lam_query=40, seed=4)
     gen_s = time.time() - t0
-    t0 = time.time()
-    g = K_.kann_hnsw_build_sparse(base, 32, 200, 4, nthreads=0)
-    build_s = time.time() - t0
     td = lambda c: (torch.from_numpy(c[0]).to(dev), torch.from_numpy(c[1].view(np.int16)).to(dev),
                     torch.from_numpy(c[2]).to(dev))
     b_d, q_d = td(base), td(qs)
+    t0 = time.time()
+    if args.sparse_host_build:
+        g = K_.kann_hnsw_build_sparse(base, 32, 200, 4, nthreads=0)
+    else:
+        g = K_.kann_hnsw_build_device_sparse(b_d[0], b_d[1], b_d[2], 30522, 32, 200, 4)
+    build_s = time.time() - t0
     idx = K_.kann_index_upload(K_.graph_to_device(g, dev), sparse=dict(indptr=b_d[0], terms=b_d[1], weights=b_d[2],
                                                                         vocab=30522))
     ngt = 1000
@@ -464,9 +470,30 @@ def run_sparse(args, n_docs=100_000):
     torch.cuda.synchronize()
     gt_s = time.time() - t0
     gt = gt.cpu().numpy()
+    # algorithmic bytes of an evaluated document: its (term, weight) pairs and
+    # its two offsets; the evaluated documents are neighbours of expanded
+    # nodes, so their mean size is taken weighted by in-degree on layer 0
+    lens = np.diff(base[0]).astype(np.float64)
+    indeg = np.bincount(g["l0"][g["l0"] >= 0].ravel(), minlength=n_docs).astype(np.float64)
+    doc_bytes = float((indeg * (lens * 6 + 16)).sum() / max(indeg.sum(), 1.0))
+    q_bytes = float(np.diff(qs[0]).mean() * 6 + 16)
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except Exception:
+        pass
+    hbm = peaks.get("hbm_gbs", 6400.0)
+    from paper_2501_06121_b300 import autotune as A_
     rows = []
     for ef in (32, 64, 128, 256, 512, 1024):
-        run = lambda: K_.kann_search_sparse(idx, q_d[0], q_d[1], q_d[2], 10, ef)
+        cnt = torch.zeros((len(qs[0]) - 1, 4), dtype=torch.int32, device=dev)
+        K_.kann_search_sparse(idx, q_d[0], q_d[1], q_d[2], 10, ef, counters=cnt, hash_bits=15)
+        torch.cuda.synchronize()
+        c = cnt.double().mean(0).cpu().numpy()
+        bq = c[0] * doc_bytes + c[1] * 64 * 4 + c[2] * doc_bytes + c[3] * 32 * 4 + q_bytes + 10 * 8
+        opts = dict(hash_bits=12 if ef <= 256 else 13)
+        run = lambda: K_.kann_search_sparse(idx, q_d[0], q_d[1], q_d[2], 10, ef, **opts)
         run()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
@@ -477,9 +504,13 @@ def run_sparse(args, n_docs=100_000):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / 5
         rows.append({"ef": ef, "qps": 1e4 / (ms / 1e3), "ms": ms,
-                     "recall@10": recall_at(ids.cpu().numpy()[:ngt], gt, 10)})
+                     "recall@10": recall_at(ids.cpu().numpy()[:ngt], gt, 10),
+                     "docs_evaluated_per_query": c[0] + c[2], "algorithmic_bytes_per_query": bq,
+                     "roofline_frac": 1e4 * bq / (ms / 1e3) / 1e9 / hbm, "launch": opts})
         print(json.dumps(rows[-1]), flush=True)
-    print(json.dumps({"workload": "sparse100k", "docs": n_docs, "data_gen_s": gen_s, "graph_build_s": build_s,
+    print(json.dumps({"workload": "sparse", "docs": n_docs, "data_gen_s": gen_s, "graph_build_s": build_s,
+                      "graph_builder": "host" if args.sparse_host_build else "device",
+                      "doc_bytes_indegree_weighted": doc_bytes, "peak_gbs": hbm,
                       "ground_truth_s_1000q": gt_s, "rows": rows}))
 
 
@@ -524,7 +555,9 @@ def main():
     ap.add_argument("--no-tune", action="store_true", help="default launch settings instead of the autotuner's")
     ap.add_argument("--serving-seconds", type=float, default=2.0)
     ap.add_argument("--serving-rates", default="5000,20000,50000,100000,200000")
-    ap.add_argument("--workload", default="sift1m", choices=["sift1m", "pq768", "sparse100k"])
+    ap.add_argument("--workload", default="sift1m", choices=["sift1m", "pq768", "sparse", "sparse100k"])
+    ap.add_argument("--sparse-n", type=int, default=1_000_000)
+    ap.add_argument("--sparse-host-build", action="store_true")
     ap.add_argument("--pq-n", type=int, default=1_000_000)
     ap.add_argument("--pq-concentration", type=float, default=0.0,
                     help="> 0: normalize(mu + sigma g) mixture instead of the kappa=50 vMF draw")
@@ -534,6 +567,8 @@ def main():
     if args.workload == "pq768":
         return run_pq768(args)
     if args.workload == "sparse100k":
+        return run_sparse(args, n_docs=100_000)
+    if args.workload == "sparse":
         return run_sparse(args)
 
     import torch
@@ -577,6 +612,18 @@ def main():
     del Xb
     gt = gt.cpu().numpy()
     gt_kth = gt_d[:, K - 1].cpu().numpy().astype(np.float64)
+    # the ground truth above is the library's tensor-core kernel; the FP64
+    # oracle's brute force recomputes a sample of it independently
+    gt_check = None
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle as O_
+        n_chk = 24
+        t_c = time.time()
+        oi, od = O_.exact_dense(X, Q[:n_chk], K, O_.L2)
+        gt_check = {"queries": n_chk, "ids_equal": bool(np.array_equal(oi, gt[:n_chk])),
+                    "dists_equal": bool(np.array_equal(od, gt_d[:n_chk].cpu().numpy().astype(np.float64))),
+                    "oracle_s": time.time() - t_c,
+                    "rule": "oracle.exact_dense (FP64 brute force, ties to the lower id) on the first queries"}
 
     # ---- ef sweep: smallest ef with recall@10 >= 0.95 (FP16 + re-rank)
     def gpu_recalls(ef):
@@ -786,6 +833,8 @@ def main():
                        "ef_sweep": {str(e): sweep[e] for e in sorted(sweep)}, "graph_build_s": build_s,
                        "graph_cached": cached,
                        "ground_truth_s": gt_s,
+                       "ground_truth": "tensor-core exact k-NN on BF16 copies (exact on this integer data)",
+                       "ground_truth_check": gt_check,
                        "batch_latency_ms": {"p50": per_sorted[len(per) // 2],
                                             "p99": per_sorted[min(len(per) - 1, int(0.99 * len(per)))]},
                        "work_per_query": {"l0_dist": c[0], "l0_expansions": c[1], "upper_dist": c[2],

@@ -49,7 +49,8 @@ extern "C" {
 #define KANN_QSTAT_FORGOT 2u    /* the visited table forgot ids (cleared, or an id found no free slot;
                                    results unaffected, the forgotten ids were evaluated again) */
 #define KANN_QSTAT_BAD_ID 4u    /* an adjacency entry >= n was met and skipped */
-#define KANN_QSTAT_QUERY_TRUNCATED 8u /* sparse query with more than 512 terms: the excess was dropped */
+#define KANN_QSTAT_QUERY_TRUNCATED 8u /* sparse query with more than 512 terms: the terms after the first
+                                         512 (in term order) were dropped */
 
 /* ---- enums --------------------------------------------------------------*/
 #define KANN_L2 0
@@ -383,6 +384,19 @@ size_t kann_hnsw_build_device_workspace_bytes(int64_t n, int d, int M, int ef_co
 int kann_hnsw_build_device(const float* d_x, int64_t n, int d, int metric, int M, int ef_construction, uint64_t seed,
                            int batch, int nthreads, const int8_t* h_level, int32_t* d_l0, int32_t* d_upper_slot,
                            int32_t* d_upper, int32_t* h_entry, void* d_ws, size_t ws_bytes, void* stream);
+
+/* The same build over sparse vectors (the sparse IP measure, Sec. 3 Table 1):
+ * device CSR d_indptr [n+1] int64, d_terms uint16 (sorted, unique per row,
+ * < vocab), d_weights FP32 with nnz = d_indptr[n] entries; distance -IP in
+ * FP32 (a merge-join of the two term lists).  The batch nodes are searched
+ * with kann_search_sparse (a node's first 512 terms).  d_ws holds
+ * kann_hnsw_build_device_sparse_workspace_bytes(n, nnz, M, ef_construction,
+ * batch) bytes (the batch queries are gathered there as a CSR). */
+size_t kann_hnsw_build_device_sparse_workspace_bytes(int64_t n, int64_t nnz, int M, int ef_construction, int batch);
+int kann_hnsw_build_device_sparse(const int64_t* d_indptr, const uint16_t* d_terms, const float* d_weights,
+                                  int64_t n, int vocab, int M, int ef_construction, uint64_t seed, int batch,
+                                  int nthreads, const int8_t* h_level, int32_t* d_l0, int32_t* d_upper_slot,
+                                  int32_t* d_upper, int32_t* h_entry, void* d_ws, size_t ws_bytes, void* stream);
 
 /* ---- diagnostics --------------------------------------------------------*/
 const char* kann_status_str(int status);

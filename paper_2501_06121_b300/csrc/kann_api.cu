@@ -239,7 +239,7 @@ int plan_shared(const kann_index_t* idx, SearchArgs& a, int& wpb) {
     return a.warp_smem + PQ_TEAM_CTL_BYTES > optin ? KANN_ENOMEM : KANN_OK;
   }
   const bool compact = a.vis_r >= 0;
-  a.warp_smem = idx->kind == 2 ? search_warp_smem_sparse(a.efcap, a.hbits, compact)
+  a.warp_smem = idx->kind == 2 ? search_warp_smem_sparse(a.efcap, a.hbits, compact, idx->sp.vocab)
                                : search_warp_smem(a.efcap, a.hbits, compact, a.expand);
   while (wpb > 1 && wpb * a.warp_smem > optin) --wpb;
   return a.warp_smem > optin ? KANN_ENOMEM : KANN_OK;

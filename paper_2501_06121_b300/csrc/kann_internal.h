@@ -94,7 +94,7 @@ int search_warp_smem(int efcap, int hbits, bool compact, int expand = 1);
 int search_warp_smem_pq(int efcap, int hbits, bool compact, int m, int lut = KANN_PQ_LUT_F32);
 // Shared memory of a PQ search team's control block (after the query's region).
 constexpr int PQ_TEAM_CTL_BYTES = 64;
-int search_warp_smem_sparse(int efcap, int hbits, bool compact);
+int search_warp_smem_sparse(int efcap, int hbits, bool compact, int vocab);
 
 // Launchers (kann_search.cu); return a cudaError_t.
 int launch_search_dense(const SearchArgs& a, int dtype, int wpb, void* stream);

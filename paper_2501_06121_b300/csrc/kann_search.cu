@@ -83,8 +83,8 @@ int search_warp_smem_pq(int efcap, int hbits, bool compact, int m, int lut) {
   return search_warp_smem(efcap, hbits, compact) + table;
 }
 
-int search_warp_smem_sparse(int efcap, int hbits, bool compact) {
-  return search_warp_smem(efcap, hbits, compact) + SP_QH * 8;
+int search_warp_smem_sparse(int efcap, int hbits, bool compact, int vocab) {
+  return search_warp_smem(efcap, hbits, compact) + sparse_query_bytes(vocab);
 }
 
 int launch_search_pq(const SearchArgs& a, int wpb, void* stream) {

@@ -527,80 +527,101 @@ struct PQBackend {
 };
 
 // ---------------------------------------------------------------------------
-// Sparse back-end (inner product over term/weight lists): the query's terms
-// are scattered into a shared-memory hash (term -> weight), then each
-// candidate document's term list is walked by a group of 8 lanes, each lane
-// summing w_q(t) * w_x(t) over its positions in order; distance = -sum.
+// Sparse back-end (inner product over term/weight lists).  The query is held
+// as a presence bitmap over the vocabulary, per-word prefix counts of set
+// bits, and its weights in term order: query terms are sorted and unique, so
+// the rank of a present term t -- the number of query terms below it, i.e.
+// prefix[t / 32] + popcount of word t / 32 below bit t % 32 -- is its index
+// in the weight array.  Each candidate document's term list is walked by a
+// group of 8 lanes, each lane summing w_q(t) * w_x(t) over its positions in
+// order; distance = -sum.  A query keeps its first 512 terms (flagged
+// otherwise); terms >= vocab never match.
 // ---------------------------------------------------------------------------
-constexpr int SP_QH = 1024;   // query table slots (queries up to 512 terms)
+constexpr int SP_QMAX = 512;  // query terms kept
 constexpr int SP_LPD = 8;     // lanes per document
+
+__host__ __device__ constexpr int sparse_words(int vocab) { return (vocab + 31) / 32; }
+// bytes of a query's tables: bitmap (4 per word), prefix counts (2 per word,
+// rounded to 4), weights
+__host__ __device__ constexpr int sparse_query_bytes(int vocab) {
+  return sparse_words(vocab) * 4 + (sparse_words(vocab) * 2 + 3) / 4 * 4 + SP_QMAX * 4;
+}
 
 struct SparseBackend {
   const SparseArgs* sp;
-  uint32_t* keys;
-  float* vals;
+  uint32_t* bm;       // [words] presence bits
+  uint16_t* pre;      // [words] set bits in the words before
+  float* qw;          // [<= SP_QMAX] weights in term order
   uint32_t trunc;
 
-  __device__ __forceinline__ uint32_t slot0(uint32_t t) const { return (t * 2654435761u) >> (32 - 10); }
-
   __device__ __forceinline__ void init(const SearchArgs& a, int qi, int lane, unsigned char* extra) {
-    keys = reinterpret_cast<uint32_t*>(extra);
-    vals = reinterpret_cast<float*>(keys + SP_QH);
-    trunc = 0;
-    for (int i = lane; i < SP_QH; i += 32) keys[i] = HEMPTY;
+    const int words = sparse_words(sp->vocab);
+    bm = reinterpret_cast<uint32_t*>(extra);
+    pre = reinterpret_cast<uint16_t*>(bm + words);
+    qw = reinterpret_cast<float*>(extra + sparse_query_bytes(sp->vocab) - SP_QMAX * 4);
+    for (int i = lane; i < words; i += 32) bm[i] = 0u;
     __syncwarp();
     const int64_t b = sp->q_indptr[qi], e = sp->q_indptr[qi + 1];
-    for (int64_t t = b + lane; t < e; t += 32) {
-      const uint32_t term = sp->q_terms[t];
-      const float w = sp->q_w[t];
-      uint32_t h = slot0(term);
-      bool done = false;
-      for (int p = 0; p < SP_QH && !done; ++p) {
-        const uint32_t old = atomicCAS(&keys[h], HEMPTY, term);
-        if (old == HEMPTY || old == term) {
-          vals[h] = w;
-          done = true;
-        }
-        h = (h + 1u) & (SP_QH - 1);
-      }
-      if (!done) trunc = 1;
+    const int nt = e - b < SP_QMAX ? (int)(e - b) : SP_QMAX;
+    trunc = e - b > SP_QMAX ? 1u : 0u;
+    for (int j = lane; j < nt; j += 32) {
+      const uint32_t t = sp->q_terms[b + j];
+      if (t < (uint32_t)sp->vocab) atomicOr(bm + (t >> 5), 1u << (t & 31));
     }
-    if (e - b > SP_QH / 2) trunc = 1;
     __syncwarp();
-  }
-
-  __device__ __forceinline__ float weight(uint32_t term) const {
-    uint32_t h = slot0(term);
-    for (int p = 0; p < SP_QH; ++p) {
-      const uint32_t k = keys[h];
-      if (k == term) return vals[h];
-      if (k == HEMPTY) return 0.f;
-      h = (h + 1u) & (SP_QH - 1);
+    // prefix counts: each lane a contiguous block of words, then a warp scan
+    const int per = (words + 31) / 32, w0 = lane * per, w1 = min(words, w0 + per);
+    int c = 0;
+    for (int i = w0; i < w1; ++i) c += __popc(bm[i]);
+    int incl = c;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(FULL, incl, o);
+      if (lane >= o) incl += v;
     }
-    return 0.f;
+    int run = incl - c;
+    for (int i = w0; i < w1; ++i) {
+      pre[i] = (uint16_t)run;
+      run += __popc(bm[i]);
+    }
+    // weights in term order (terms >= vocab, which never match, keep their
+    // slots so that the ranks of the others stay their positions)
+    for (int j = lane; j < nt; j += 32) qw[j] = sp->q_w[b + j];
+    __syncwarp();
   }
 
   __device__ __forceinline__ void dists(const SearchArgs&, const int* cid, int cnt, u64* ck, int lane) {
     const int sub = lane & (SP_LPD - 1), grp = lane / SP_LPD;
     constexpr int DPI = 32 / SP_LPD;  // documents per warp iteration
+    const uint32_t vocab = (uint32_t)sp->vocab;
     for (int base = 0; base < cnt; base += DPI) {
       const int r = base + grp;
       const int id = r < cnt ? cid[r] : -1;
       float acc = 0.f;
       if (id >= 0) {
-        const int64_t b = __ldg(sp->indptr + id), e = __ldg(sp->indptr + id + 1);
-        for (int64_t t0 = b + sub; t0 < e; t0 += 4 * SP_LPD) {
+        const int64_t b = __ldg(sp->indptr + id);
+        const int len = (int)(__ldg(sp->indptr + id + 1) - b);
+        const uint16_t* tp = sp->terms + b;
+        const float* wp = sp->w + b;
+        for (int t0 = sub; t0 < len; t0 += 4 * SP_LPD) {
           uint32_t tm[4];
           float wx[4];
 #pragma unroll
           for (int u = 0; u < 4; ++u) {
-            const int64_t t = t0 + u * SP_LPD;
-            tm[u] = t < e ? (uint32_t)__ldg(sp->terms + t) : HEMPTY;
-            wx[u] = t < e ? __ldg(sp->w + t) : 0.f;
+            const int t = t0 + u * SP_LPD;
+            tm[u] = t < len ? (uint32_t)__ldg(tp + t) : 0xffffffffu;
+            wx[u] = t < len ? __ldg(wp + t) : 0.f;
           }
 #pragma unroll
-          for (int u = 0; u < 4; ++u)
-            if (tm[u] != HEMPTY) acc = fmaf(weight(tm[u]), wx[u], acc);
+          for (int u = 0; u < 4; ++u) {
+            const uint32_t t = tm[u];
+            if (t < vocab) {
+              const uint32_t wd = bm[t >> 5];
+              if ((wd >> (t & 31)) & 1u) {
+                const int rk = pre[t >> 5] + __popc(wd & ((1u << (t & 31)) - 1u));
+                acc = fmaf(qw[rk], wx[u], acc);
+              }
+            }
+          }
         }
       }
       for (int o = SP_LPD >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);

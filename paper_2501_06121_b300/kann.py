@@ -99,6 +99,8 @@ def _lib():
             "kann_pq_encode": (I, [P, I64, I, I, P, P, P]),
             "kann_hnsw_build_device_workspace_bytes": (SZ, [I64, I, I, I, I]),
             "kann_hnsw_build_device": (I, [P, I64, I, I, I, I, U64, I, I, P, P, P, P, P, P, SZ, P]),
+            "kann_hnsw_build_device_sparse_workspace_bytes": (SZ, [I64, I64, I, I, I]),
+            "kann_hnsw_build_device_sparse": (I, [P, P, P, I64, I, I, I, U64, I, I, P, P, P, P, P, P, SZ, P]),
             "kann_status_str": (ctypes.c_char_p, [I]),
             "kann_last_cuda_error": (I, []),
         }
@@ -454,6 +456,33 @@ def kann_hnsw_build_device(x, metric, M, ef_construction, seed, batch=0, nthread
         _check("kann_hnsw_build_device", _lib().kann_hnsw_build_device(
             _dev(x), n, d, metric, M, ef_construction, seed, batch, nthreads, _vp(level), _dev(d_l0), _dev(d_us),
             _dev(d_up), ctypes.byref(entry), _dev(ws), ws.numel(), _stream(stream)))
+        torch.cuda.synchronize()
+    if L > 0:
+        up = d_up.cpu().numpy()
+    return dict(n=n, M=M, M0=2 * M, max_level=L, entry=entry.value, level=level, l0=d_l0.cpu().numpy(),
+                upper_slot=d_us.cpu().numpy(), upper=up)
+
+
+def kann_hnsw_build_device_sparse(indptr, terms, weights, vocab, M, ef_construction, seed, batch=0, nthreads=0,
+                                  stream=None):
+    """HNSW over a device CSR (indptr int64 [n+1], terms int16-view of uint16,
+    weights float32) with the layer-0 insertions on the GPU; returns the
+    serialised graph as a dict of numpy arrays."""
+    _require_cuda(indptr, terms, weights)
+    n = indptr.shape[0] - 1
+    nnz = int(indptr[-1].item())
+    level, L, nu, l0, us, up = _graph_buffers(n, M, seed)
+    dev = indptr.device
+    with torch.cuda.device(dev):
+        d_l0 = torch.empty((n, 2 * M), dtype=torch.int32, device=dev)
+        d_us = torch.empty(n, dtype=torch.int32, device=dev)
+        d_up = torch.empty(up.shape, dtype=torch.int32, device=dev)
+        wsb = int(_lib().kann_hnsw_build_device_sparse_workspace_bytes(n, nnz, M, ef_construction, batch))
+        ws = torch.empty(max(wsb, 16), dtype=torch.uint8, device=dev)
+        entry = ctypes.c_int32()
+        _check("kann_hnsw_build_device_sparse", _lib().kann_hnsw_build_device_sparse(
+            _dev(indptr), _dev(terms), _dev(weights), n, vocab, M, ef_construction, seed, batch, nthreads, _vp(level),
+            _dev(d_l0), _dev(d_us), _dev(d_up), ctypes.byref(entry), _dev(ws), ws.numel(), _stream(stream)))
         torch.cuda.synchronize()
     if L > 0:
         up = d_up.cpu().numpy()

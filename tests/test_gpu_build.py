@@ -91,3 +91,28 @@ def test_device_builder_all_nodes_on_layer_zero_and_tiny_inputs():
             ids, _ = K.kann_search(idx, dev(X[:5]), 1, max(n, 1))
             torch.cuda.synchronize()
             assert np.array_equal(ids.cpu().numpy()[:, 0], ei[:, 0])  # ef >= n: exact
+
+
+def test_device_builder_sparse_invariants_and_recall():
+    # sparse IP (the Splade-shaped measure): the host builder's sparse
+    # invariants (reachability is not bounded for -IP graphs, whose Zipf hubs
+    # win most comparisons) and recall within 0.01 of a host-built graph
+    base, qs = G.sparse_zipf(8000, 200, vocab=3000, lam_doc=40, lam_query=12, seed=31)
+    td = lambda c: (dev(c[0]), dev(c[1].view(np.int16)), dev(c[2]))
+    b_d = td(base)
+    gd = K.kann_hnsw_build_device_sparse(b_d[0], b_d[1], b_d[2], 3000, 16, 100, 31)
+    assert graph_problems(gd, max_unreachable=1.0) == []
+    lv, L, nu = K.kann_hnsw_levels(8000, 16, 31)
+    assert np.array_equal(gd["level"], lv)
+    gh = K.kann_hnsw_build_sparse(base, 16, 100, 31, nthreads=0)
+    gt, _ = O.exact_sparse(base, qs, 10)
+    q_d = td(qs)
+    for ef in (32, 64, 128):
+        rs = []
+        for g in (gh, gd):
+            idx = K.kann_index_upload(K.graph_to_device(g), sparse=dict(indptr=b_d[0], terms=b_d[1], weights=b_d[2],
+                                                                        vocab=3000))
+            ids, _ = K.kann_search_sparse(idx, q_d[0], q_d[1], q_d[2], 10, ef)
+            torch.cuda.synchronize()
+            rs.append(recall(ids.cpu().numpy(), gt, 10))
+        assert rs[1] >= rs[0] - 0.01, (ef, rs)

@@ -40,12 +40,18 @@ int pow2_at_least(int x) {
 
 }  // namespace
 
+// Every warp's (team's) region starts at a multiple of its size, and its
+// 8-byte beam keys and 16-byte visited-table rows need that start aligned:
+// region sizes are rounded up to 128 bytes.
+int round_region(int bytes) { return (bytes + 127) / 128 * 128; }
+
 int search_warp_smem(int efcap, int hbits, bool compact, int expand) {
-  return efcap * 8 + cand_keys(expand) * 8 + 64 * expand * 4 + ((compact ? 2 : 4) << hbits);
+  return round_region(efcap * 8 + cand_keys(expand) * 8 + 64 * expand * 4 + ((compact ? 2 : 4) << hbits));
 }
 
 int launch_search_dense(const SearchArgs& a, int dtype, int wpb, void* stream) {
   if (a.nq == 0) return 0;
+  if (a.warp_smem % 16 != 0) return (int)cudaErrorInvalidValue;  // regions must stay 16-byte aligned
   const int cplt = pow2_at_least((a.nchunks + a.lpr - 1) / a.lpr);
   const int lpr_exact = a.nchunks == a.lpr * cplt ? a.lpr : 0;
   SearchKernelFn fn = nullptr;
@@ -80,15 +86,16 @@ int launch_search_dense(const SearchArgs& a, int dtype, int wpb, void* stream) {
 int search_warp_smem_pq(int efcap, int hbits, bool compact, int m, int lut) {
   // uint8 table: the entries plus the subspace minima and ranges (8 m bytes)
   const int table = lut == KANN_PQ_LUT_U8 ? m * 256 + 8 * m : m * 256 * (lut == KANN_PQ_LUT_F16 ? 2 : 4);
-  return search_warp_smem(efcap, hbits, compact) + table;
+  return round_region(search_warp_smem(efcap, hbits, compact) + table);
 }
 
 int search_warp_smem_sparse(int efcap, int hbits, bool compact, int vocab) {
-  return search_warp_smem(efcap, hbits, compact) + sparse_query_bytes(vocab);
+  return round_region(search_warp_smem(efcap, hbits, compact) + sparse_query_bytes(vocab));
 }
 
 int launch_search_pq(const SearchArgs& a, int wpb, void* stream) {
   if (a.nq == 0) return 0;
+  if (a.warp_smem % 16 != 0) return (int)cudaErrorInvalidValue;  // regions must stay 16-byte aligned
   const int cplt = pow2_at_least((a.nchunks + a.lpr - 1) / a.lpr);
   SearchKernelFn fn = nullptr;
   static_assert(PQ_LUT_F16 == KANN_PQ_LUT_F16 && PQ_LUT_U8 == KANN_PQ_LUT_U8, "table formats");
@@ -127,6 +134,7 @@ int launch_search_pq(const SearchArgs& a, int wpb, void* stream) {
 
 int launch_search_sparse(const SearchArgs& a, const SparseArgs& sp, int wpb, void* stream) {
   if (a.nq == 0) return 0;
+  if (a.warp_smem % 16 != 0) return (int)cudaErrorInvalidValue;  // regions must stay 16-byte aligned
   const size_t smem = (size_t)wpb * a.warp_smem;
   cudaError_t e = cudaFuncSetAttribute(search_sparse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return (int)e;

@@ -317,34 +317,93 @@ def run_reference(args):
 
 
 def run_serving(g, Xd, Q, dev, args):
-    """Continuous-batching serving: two resident indices (this 1M x 128 set and
-    a 10k x 128 Gaussian-mixture set), both with E4M3 per-vector-scaled
-    traversal + FP32 re-rank; Poisson arrivals at each rate, k in {10, 100},
-    ef uniform in 64..512; latency = completion seen on the host - arrival."""
+    """Continuous-batching serving of two resident indices: the 10k x 128
+    Gaussian mixture (32 clusters, sigma 5; M=16, efC=100) and a 768-d index
+    (`--serving-768-n` unit vectors, inner product, the concentrated mixture
+    normalize(mu + 0.04 g) over 1,024 directions, M=32, efC=200, graph built
+    on the device), both with FP8 E4M3 per-vector-scaled traversal and an FP32
+    re-rank of the ef candidates (`--serving-pq`: the 768-d index also served
+    with PQ m=192 codes, uint8 table, re-rank of 100, as a second run).
+    Poisson arrivals at each rate for `--serving-seconds`, k in {10, 100},
+    ef uniform in 64..512; latency = completion seen on the host - arrival.
+    Admission by device memory (pages created and released within
+    `--serving-memory` bytes).  For each index the served form's recall@10 and
+    the plain FP32 traversal's at ef 128, the difference, and the largest
+    relative error of the served distances against the FP64 oracle's
+    distances of the same ids, on a sample of queries."""
+    import oracle as O
+    import torch
     from paper_2501_06121_b300 import datagen as G
     from paper_2501_06121_b300 import kann as K_
     from paper_2501_06121_b300 import serving as S
-    c8, s8 = K_.kann_quantize(Xd, K_.KANN_E4M3)
-    big = K_.kann_index_upload(K_.graph_to_device(g, dev), vectors=c8, dtype=K_.KANN_E4M3, scale=s8,
-                               metric=K_.KANN_L2, rerank=Xd)
     X1, Q1 = G.gaussian_mixture(10000, 1000, d=128, clusters=32, sigma=5.0, seed=1)
     g1 = K_.kann_hnsw_build_dense(X1, K_.KANN_L2, 16, 100, 1, nthreads=0)
     X1d = torch_from(X1, dev)
     c1, s1 = K_.kann_quantize(X1d, K_.KANN_E4M3)
     small = K_.kann_index_upload(K_.graph_to_device(g1, dev), vectors=c1, dtype=K_.KANN_E4M3, scale=s1,
                                  metric=K_.KANN_L2, rerank=X1d)
+    n7 = args.serving_768_n
+    t0 = time.time()
+    X7, Q7 = G.vmf_mixture(n7, 10_000, d=768, clusters=1024, kappa=50.0, seed=3, concentration=0.04)
+    X7d = torch_from(X7, dev)
+    del X7
+    g7 = K_.kann_hnsw_build_device(X7d, K_.KANN_IP, 32, 200, 3)
+    build7 = time.time() - t0
+    gd7 = K_.graph_to_device(g7, dev)
+    c7, s7 = K_.kann_quantize(X7d, K_.KANN_E4M3)
+    big = K_.kann_index_upload(gd7, vectors=c7, dtype=K_.KANN_E4M3, scale=s7, metric=K_.KANN_IP, rerank=X7d)
+    plain = {"10kx128": K_.kann_index_upload(K_.graph_to_device(g1, dev), vectors=X1d, metric=K_.KANN_L2),
+             "768": K_.kann_index_upload(gd7, vectors=X7d, metric=K_.KANN_IP)}
+
+    def accuracy(name, index, Xd_, Qh, metric, oracle_X, n=200, ef=128, opts=None):
+        Qs = torch_from(Qh[:n], dev)
+        gt, _ = K_.kann_exact_knn(Qs, Xd_, 10, metric)
+        ids, d = K_.kann_search_ex(index, Qs, 10, ef, **(opts or dict(rerank=-1)))
+        pi, _ = K_.kann_search_ex(plain[name], Qs, 10, ef)
+        torch.cuda.synchronize()
+        ids, d, gt, pi = ids.cpu().numpy(), d.cpu().numpy(), gt.cpu().numpy(), pi.cpu().numpy()
+        ref = O.dist_dense(oracle_X, Qh[:n], np.maximum(ids, 0), metric)
+        mag = np.abs(ref) if metric == K_.KANN_L2 else np.einsum(
+            "qd,qkd->qk", np.abs(Qh[:n].astype(np.float64)), np.abs(oracle_X.astype(np.float64)[np.maximum(ids, 0)]))
+        err = np.abs(d.astype(np.float64) - ref) / np.maximum(np.maximum(np.abs(ref), mag), 1e-30)
+        r_s, r_p = recall_at(ids, gt), recall_at(pi, gt)
+        return {"ef": ef, "queries": n, "recall@10_served": r_s, "recall@10_fp32_traversal": r_p,
+                "recall_delta": r_s - r_p, "max_rel_dist_error_vs_fp64_oracle": float(err[ids >= 0].max())}
+
+    acc = {"10kx128": accuracy("10kx128", small, X1d, Q1, K_.KANN_L2, X1),
+           "768": accuracy("768", big, X7d, Q7, K_.KANN_IP, X7d.cpu().numpy())}
     spec = dict(kmax=100, efmax=512, opts=dict(rerank=-1))
-    srv = S.SearchServer({"1Mx128": dict(spec, index=big, d=128), "10kx128": dict(spec, index=small, d=128)},
-                         slots_per_index=3, slot_capacity=2048, memory_budget=256 << 20)
-    out = {"indices": "1M x 128 integer mixture + 10k x 128 Gaussian mixture, E4M3 traversal + FP32 re-rank (R = ef)",
-           "k": [10, 100], "ef": [64, 512], "seconds_per_rate": args.serving_seconds,
-           "slot_device_bytes": srv.device_bytes, "rates": []}
-    for i, rate in enumerate(float(r) for r in args.serving_rates.split(",")):
-        reqs = S.poisson_requests(rate, args.serving_seconds, {"1Mx128": Q, "10kx128": Q1}, seed=100 + i)
-        done = srv.run(reqs, time_limit=args.serving_seconds * 3 + 5)
-        summ = S.latency_summary(done, max(r["t_done"] for r in done) if done else 1.0)
-        summ.update(offered_qps=rate, requests=len(reqs))
-        out["rates"].append(summ)
+    runs = [("e4m3_rerank", {"10kx128": dict(spec, index=small, d=128), "768": dict(spec, index=big, d=768)})]
+    if args.serving_pq:
+        cb = K_.kann_pq_train(X7d[:min(n7, 100_000)].contiguous(), 192, iters=25, seed=3)
+        codes = K_.kann_pq_encode(X7d, cb)
+        pq7 = K_.kann_index_upload(gd7, pq=dict(codes=codes, codebooks=cb, metric=K_.KANN_IP), rerank=X7d)
+        acc["768_pq"] = accuracy("768", pq7, X7d, Q7, K_.KANN_IP, X7d.cpu().numpy(),
+                                 opts=dict(rerank=100, pq_lut=K_.KANN_PQ_LUT_U8))
+        runs.append(("pq_u8_rerank100", {"10kx128": dict(spec, index=small, d=128),
+                                         "768": dict(kmax=100, efmax=512, index=pq7, d=768,
+                                                     opts=dict(rerank=100, pq_lut=K_.KANN_PQ_LUT_U8))}))
+    out = {"indices": {"10kx128": "10k x 128 Gaussian mixture, L2, M=16, efC=100",
+                       "768": "%d x 768 unit vectors (concentrated mixture), IP, M=32, efC=200, device-built graph "
+                              "(%.0f s incl. data)" % (n7, build7)},
+           "traversal": "FP8 E4M3 per-vector scale + FP32 re-rank (R = ef)", "k": [10, 100], "ef": [64, 512],
+           "seconds_per_rate": args.serving_seconds, "memory_budget": args.serving_memory,
+           "accuracy_vs_fp64_oracle": acc, "runs": []}
+    Q7h = Q7
+    for run_name, indices in runs:
+        srv = S.SearchServer(indices, page_capacity=2048, memory_budget=args.serving_memory, max_pages=8)
+        srv.prepare({"10kx128": 2, "768": 2})
+        res = {"run": run_name, "page_capacity": srv.caps, "rates": []}
+        for i, rate in enumerate(float(r) for r in args.serving_rates.split(",")):
+            reqs = S.poisson_requests(rate, args.serving_seconds, {"10kx128": Q1, "768": Q7h}, seed=100 + i)
+            done = srv.run(reqs, time_limit=args.serving_seconds * 3 + 10)
+            summ = S.latency_summary(done, max(r["t_done"] for r in done) if done else 1.0)
+            summ.update(offered_qps=rate, requests=len(reqs), status=S.status_counts(done))
+            res["rates"].append(summ)
+            print(json.dumps({"serving": run_name, **summ}), flush=True)
+        res["memory"] = dict(srv.stats)
+        out["runs"].append(res)
+        del srv
     return out
 
 
@@ -553,7 +612,10 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-curve", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="default launch settings instead of the autotuner's")
-    ap.add_argument("--serving-seconds", type=float, default=2.0)
+    ap.add_argument("--serving-seconds", type=float, default=8.0)
+    ap.add_argument("--serving-768-n", type=int, default=1_000_000)
+    ap.add_argument("--serving-pq", action="store_true", help="also serve the 768-d index with PQ codes")
+    ap.add_argument("--serving-memory", type=int, default=48 << 20)
     ap.add_argument("--serving-rates", default="5000,20000,50000,100000,200000")
     ap.add_argument("--workload", default="sift1m", choices=["sift1m", "pq768", "sparse", "sparse100k"])
     ap.add_argument("--sparse-n", type=int, default=1_000_000)

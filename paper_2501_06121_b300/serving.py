@@ -1,20 +1,26 @@
 """Continuous-batching search server over resident indices.
 
-Requests (index, query, k, ef) arrive over time.  The server keeps a fixed
-set of batch slots per index, each with its own CUDA stream, device and
-pinned host buffers and a CUDA graph of one persistent, work-stealing
-`kann_search_batch` launch (mixed k and ef per query, the batch size read
-from device memory so that one graph serves any batch up to the slot's
-capacity).  Whenever a slot is free, the requests that have arrived and are
-still waiting are admitted into it (up to its capacity) and launched; slots
-run concurrently on their streams, so requests that arrive while earlier
-batches are on the GPU start as soon as a slot frees up instead of waiting
-for a global batch boundary.
+Requests (index, query, k, ef) arrive over time.  The server runs them in
+batches on *pages*: a page belongs to one index and holds a CUDA stream,
+device and pinned host buffers for up to `capacity` queries (queries, per-query
+k and ef, outputs, per-query status words) and a CUDA graph of one
+persistent, work-stealing `kann_search_batch` launch that reads the batch size
+from device memory, so one graph serves any batch up to the capacity.
 
-Admission is by device memory: the slots are sized up front from a byte
-budget (queries, per-query k/ef, outputs), and a request is admitted only
-into a slot whose buffers it fits.  Every search step runs in the library's
-kernels; this module only stages buffers, replays graphs and keeps time.
+Admission is by device memory: every page counts the bytes
+`kann_search_workspace_bytes` gives for its capacity and settings, and the
+pages alive at any time never exceed the memory budget.  When requests of an
+index are waiting and no page of that index is idle, the server creates one if
+the budget has room, else releases the least recently used idle page of
+another index and takes its memory, else the requests wait until a running
+batch finishes and frees its page.  So arriving requests are admitted as
+memory (not a fixed partition of it) frees up, batches of different indices
+overlap on the device on their own streams, and a burst on one index can use
+the memory that idle indices are not using.  Every finished request carries
+its status word (KANN_QSTAT_* bits); the run's summary counts them.
+
+Every search step runs in the library's kernels; this module only stages
+buffers, replays graphs and keeps time.
 """
 import collections
 import time
@@ -25,37 +31,45 @@ import torch
 from . import kann as K
 
 
-class _Slot:
-    def __init__(self, index, d, kmax, efmax, cap, device, opts):
-        self.index, self.d, self.kmax, self.efmax, self.cap = index, d, kmax, efmax, cap
+class _Page:
+    def __init__(self, name, spec, cap, device, opts):
+        self.name, self.index, self.d = name, spec["index"], spec["d"]
+        self.kmax, self.efmax, self.cap = spec["kmax"], spec["efmax"], cap
         self.stream = torch.cuda.Stream(device=device)
         f32, i32 = torch.float32, torch.int32
-        self.q = torch.zeros((cap, d), dtype=f32, device=device)
+        self.q = torch.zeros((cap, self.d), dtype=f32, device=device)
         self.k = torch.ones(cap, dtype=i32, device=device)
-        self.ef = torch.full((cap,), kmax, dtype=i32, device=device)
+        self.ef = torch.full((cap,), self.kmax, dtype=i32, device=device)
         self.n = torch.zeros(1, dtype=i32, device=device)
         self.counter = torch.zeros(1, dtype=i32, device=device)
-        self.ids = torch.empty((cap, kmax), dtype=i32, device=device)
-        self.dists = torch.empty((cap, kmax), dtype=f32, device=device)
-        self.h_q = torch.zeros((cap, d), dtype=f32).pin_memory()
+        self.ids = torch.empty((cap, self.kmax), dtype=i32, device=device)
+        self.dists = torch.empty((cap, self.kmax), dtype=f32, device=device)
+        self.status = torch.zeros(cap, dtype=i32, device=device)
+        self.h_q = torch.zeros((cap, self.d), dtype=f32).pin_memory()
         self.h_k = torch.ones(cap, dtype=i32).pin_memory()
-        self.h_ef = torch.full((cap,), kmax, dtype=i32).pin_memory()
+        self.h_ef = torch.full((cap,), self.kmax, dtype=i32).pin_memory()
         self.h_n = torch.zeros(1, dtype=i32).pin_memory()
-        self.h_ids = torch.empty((cap, kmax), dtype=i32).pin_memory()
-        self.h_dists = torch.empty((cap, kmax), dtype=f32).pin_memory()
+        self.h_ids = torch.empty((cap, self.kmax), dtype=i32).pin_memory()
+        self.h_dists = torch.empty((cap, self.kmax), dtype=f32).pin_memory()
+        self.h_status = torch.zeros(cap, dtype=i32).pin_memory()
         self.np_q, self.np_k, self.np_ef = self.h_q.numpy(), self.h_k.numpy(), self.h_ef.numpy()
-        self.np_ids, self.np_dists = self.h_ids.numpy(), self.h_dists.numpy()
+        self.np_ids, self.np_dists, self.np_status = self.h_ids.numpy(), self.h_dists.numpy(), self.h_status.numpy()
         self.opts = opts
         self.event = torch.cuda.Event()
-        self.busy = None  # list of request records in flight
-        self.graph = None
+        self.busy = None  # the requests in flight
+        self.last_used = 0.0
+        self.bytes = K.kann_search_workspace_bytes(self.index, cap, self.kmax, self.efmax, **self._size_opts())
+        self._capture()
+
+    def _size_opts(self):
+        return {k: v for k, v in self.opts.items() if k not in ("status", "counters", "work_counter", "n_device")}
 
     def _launch(self):
         K.kann_search_batch(self.index, self.q, self.k, self.ef, kmax=self.kmax, efmax=self.efmax, ids=self.ids,
                             dists=self.dists, stream=self.stream, work_counter=self.counter, n_device=self.n,
-                            **self.opts)
+                            status=self.status, **self.opts)
 
-    def capture(self):
+    def _capture(self):
         # warm the launch once (sets kernel attributes), then capture it
         self.h_n[0] = 1
         with torch.cuda.stream(self.stream):
@@ -66,9 +80,6 @@ class _Slot:
         with torch.cuda.graph(self.graph, stream=self.stream, capture_error_mode="relaxed"):
             self._launch()
         self.stream.synchronize()
-
-    def bytes(self):
-        return K.kann_search_workspace_bytes(self.index, self.cap, self.kmax, self.efmax)
 
     def submit(self, reqs):
         n = len(reqs)
@@ -84,53 +95,106 @@ class _Slot:
             self.graph.replay()
             self.h_ids[:n].copy_(self.ids[:n], non_blocking=True)
             self.h_dists[:n].copy_(self.dists[:n], non_blocking=True)
+            self.h_status[:n].copy_(self.status[:n], non_blocking=True)
             self.event.record(self.stream)
         self.busy = reqs
 
     def poll(self):
-        """Finished requests (with results filled in), or None if still running."""
+        """Finished requests (with results and status filled in), or None if
+        still running."""
         if self.busy is None or not self.event.query():
             return None
         reqs, self.busy = self.busy, None
         for i, r in enumerate(reqs):
             r["ids"] = self.np_ids[i, :r["k"]].copy()
             r["dists"] = self.np_dists[i, :r["k"]].copy()
+            r["status"] = int(self.np_status[i])
         return reqs
 
 
 class SearchServer:
-    """indices: {name: dict(index=Index, d=..., kmax=..., efmax=...)}.
-    memory_budget: device bytes for all slot buffers; slots_per_index and
-    slot_capacity are reduced until the slots fit."""
+    """indices: {name: dict(index=Index, d=..., kmax=..., efmax=..., opts={...})}.
 
-    def __init__(self, indices, slots_per_index=3, slot_capacity=1024, memory_budget=1 << 30, device="cuda",
+    page_capacity: queries per batch (halved for an index until one page fits
+    the budget); memory_budget: device bytes all live pages may count
+    together (each page counts kann_search_workspace_bytes of its capacity);
+    max_pages: streams in flight at most."""
+
+    def __init__(self, indices, page_capacity=1024, memory_budget=1 << 30, max_pages=16, device="cuda",
                  search_opts=None):
-        self.slots = collections.OrderedDict()
+        self.specs, self.caps, self.page_bytes = {}, {}, {}
+        self.device, self.budget, self.max_pages = device, memory_budget, max_pages
         for name, spec in indices.items():
-            cap = slot_capacity
-            per = lambda c: K.kann_search_workspace_bytes(spec["index"], c, spec["kmax"], spec["efmax"])
-            if per(cap) == 0:
+            opts = dict(search_opts or {}, **spec.get("opts", {}))
+            opts.pop("persistent", None)  # pages always launch the persistent form
+            size = lambda c: K.kann_search_workspace_bytes(spec["index"], c, spec["kmax"], spec["efmax"], **opts)
+            cap = page_capacity
+            if size(cap) == 0:
                 raise ValueError("index %r cannot run a search with kmax=%d efmax=%d" % (name, spec["kmax"],
                                                                                         spec["efmax"]))
-            while cap > 16 and per(cap) * slots_per_index * len(indices) > memory_budget:
+            while cap > 16 and size(cap) > memory_budget:
                 cap //= 2
-            self.slots[name] = [_Slot(spec["index"], spec["d"], spec["kmax"], spec["efmax"], cap, device,
-                                      dict(search_opts or {}, **spec.get("opts", {})))
-                                for _ in range(slots_per_index)]
-        for ss in self.slots.values():
-            for s in ss:
-                s.capture()
-        self.device_bytes = sum(s.bytes() for ss in self.slots.values() for s in ss)
+            if size(cap) > memory_budget:
+                raise ValueError("index %r: a page of %d queries needs %d bytes, above the budget" %
+                                 (name, cap, size(cap)))
+            self.specs[name] = dict(spec, opts=opts)
+            self.caps[name] = cap
+            self.page_bytes[name] = size(cap)
+        self.pages = []
+        self.stats = {"pages_created": 0, "pages_released": 0, "admissions_waited_for_memory": 0,
+                      "peak_bytes": 0}
 
+    # ---- pages
+    def live_bytes(self):
+        return sum(p.bytes for p in self.pages)
+
+    def _new_page(self, name):
+        p = _Page(name, self.specs[name], self.caps[name], self.device, self.specs[name]["opts"])
+        self.pages.append(p)
+        self.stats["pages_created"] += 1
+        self.stats["peak_bytes"] = max(self.stats["peak_bytes"], self.live_bytes())
+        return p
+
+    def _page_for(self, name):
+        """An idle page of index `name`, made room for within the budget, or
+        None when the memory is taken by running batches."""
+        for p in self.pages:
+            if p.name == name and p.busy is None:
+                return p
+        need = self.page_bytes[name]
+        if self.live_bytes() + need <= self.budget and len(self.pages) < self.max_pages:
+            return self._new_page(name)
+        # release idle pages of other indices, least recently used first
+        idle = sorted((p for p in self.pages if p.busy is None and p.name != name), key=lambda p: p.last_used)
+        for p in idle:
+            if self.live_bytes() + need <= self.budget and len(self.pages) < self.max_pages:
+                break
+            self.pages.remove(p)
+            self.stats["pages_released"] += 1
+        if self.live_bytes() + need <= self.budget and len(self.pages) < self.max_pages:
+            return self._new_page(name)
+        return None
+
+    def prepare(self, counts=None):
+        """Create pages up front (counts: {name: pages}) so that the first
+        requests do not pay for a graph capture."""
+        for name, c in (counts or {n: 1 for n in self.specs}).items():
+            for _ in range(c):
+                if self.live_bytes() + self.page_bytes[name] > self.budget or len(self.pages) >= self.max_pages:
+                    break
+                self._new_page(name)
+
+    # ---- serving
     def run(self, requests, time_limit=None):
         """requests: list of dict(t=arrival seconds from start, index=name,
         query=float32[d], k=int, ef=int).  Serves them in arrival order,
         sleeping until each arrives; returns them with 'ids', 'dists',
-        't_done' (seconds from start) and 'latency' (t_done - t)."""
+        'status', 't_done' (seconds from start) and 'latency' (t_done - t)."""
         reqs = sorted(requests, key=lambda r: r["t"])
-        pending = {name: collections.deque() for name in self.slots}
+        pending = {name: collections.deque() for name in self.specs}
         nxt, done = 0, []
         t0 = time.perf_counter()
+        waited = set()
         while len(done) < len(reqs):
             now = time.perf_counter() - t0
             if time_limit is not None and now > time_limit:
@@ -138,25 +202,40 @@ class SearchServer:
             while nxt < len(reqs) and reqs[nxt]["t"] <= now:
                 pending[reqs[nxt]["index"]].append(reqs[nxt])
                 nxt += 1
-            for name, ss in self.slots.items():
-                for s in ss:
-                    fin = s.poll()
-                    if fin is not None:
-                        tnow = time.perf_counter() - t0
-                        for r in fin:
-                            r["t_done"] = tnow
-                            r["latency"] = tnow - r["t"]
-                        done.extend(fin)
-                    if s.busy is None and pending[name]:
-                        take = [pending[name].popleft() for _ in range(min(s.cap, len(pending[name])))]
-                        s.submit(take)
-            if nxt < len(reqs) and all(s.busy is None for ss in self.slots.values() for s in ss) and \
-                    not any(pending.values()):
+            for p in self.pages:
+                fin = p.poll()
+                if fin is not None:
+                    tnow = time.perf_counter() - t0
+                    p.last_used = tnow
+                    for r in fin:
+                        r["t_done"] = tnow
+                        r["latency"] = tnow - r["t"]
+                    done.extend(fin)
+            # admit: the index whose oldest waiting request is oldest goes first
+            order = sorted((q[0]["t"], name) for name, q in pending.items() if q)
+            for _, name in order:
+                q = pending[name]
+                while q:
+                    page = self._page_for(name)
+                    if page is None:
+                        if id(q[0]) not in waited:
+                            waited.add(id(q[0]))
+                            self.stats["admissions_waited_for_memory"] += 1
+                        break
+                    page.submit([q.popleft() for _ in range(min(page.cap, len(q)))])
+            if nxt < len(reqs) and all(p.busy is None for p in self.pages) and not any(pending.values()):
                 # idle: sleep until the next arrival
                 wait = reqs[nxt]["t"] - (time.perf_counter() - t0)
                 if wait > 0:
                     time.sleep(min(wait, 0.002))
         return done
+
+
+def status_counts(done):
+    """How many finished requests carry each KANN_QSTAT_* bit."""
+    names = {"hop_cap": K.KANN_QSTAT_HOPCAP, "forgot": K.KANN_QSTAT_FORGOT, "bad_id": K.KANN_QSTAT_BAD_ID,
+             "query_truncated": K.KANN_QSTAT_QUERY_TRUNCATED}
+    return {n: int(sum(1 for r in done if r.get("status", 0) & b)) for n, b in names.items()}
 
 
 def poisson_requests(rate, duration, index_queries, k_choices=(10, 100), ef_range=(64, 512), seed=0):

@@ -90,7 +90,7 @@ def test_server_results_equal_alone_and_in_the_mix(two_indices):
     idx_b, Qb, _ = two_indices["b"]
     indices = {"a": dict(index=idx_a, d=128, kmax=100, efmax=512),
                "b": dict(index=idx_b, d=64, kmax=100, efmax=512, opts=dict(rerank=-1))}
-    srv = S.SearchServer(indices, slots_per_index=3, slot_capacity=128)
+    srv = S.SearchServer(indices, page_capacity=128, max_pages=6)
     reqs = S.poisson_requests(20000.0, 0.05, {"a": Qa, "b": Qb}, seed=5)
     done = srv.run(reqs, time_limit=30.0)
     assert len(done) == len(reqs)
@@ -99,8 +99,33 @@ def test_server_results_equal_alone_and_in_the_mix(two_indices):
         o = dict(rerank=-1) if r["index"] == "b" else {}
         si, sd = single(idx, r["query"], r["k"], r["ef"], **o)
         assert np.array_equal(si, r["ids"]) and np.array_equal(sd, r["dists"])
+    assert all(r["status"] & K.KANN_QSTAT_BAD_ID == 0 for r in done)
     summ = S.latency_summary(done, 0.05)
     assert summ["completed"] == len(reqs) and summ["p99_ms"] >= summ["p50_ms"] > 0
+
+
+def test_server_admits_by_memory_as_it_frees(two_indices):
+    # a budget with room for two pages in all: bursts on two indices take the
+    # memory in turn (pages of the idle index are released), and every result
+    # still equals a single call
+    idx_a, Qa, _ = two_indices["a"]
+    idx_b, Qb, _ = two_indices["b"]
+    spec = {"a": dict(index=idx_a, d=128, kmax=10, efmax=128), "b": dict(index=idx_b, d=64, kmax=10, efmax=128)}
+    pa = K.kann_search_workspace_bytes(idx_a, 64, 10, 128)
+    pb = K.kann_search_workspace_bytes(idx_b, 64, 10, 128)
+    srv = S.SearchServer(spec, page_capacity=64, memory_budget=max(pa, pb) * 2, max_pages=8)
+    ra = S.poisson_requests(200000.0, 0.01, {"a": Qa}, k_choices=(10,), ef_range=(16, 128), seed=7)
+    rb = S.poisson_requests(200000.0, 0.01, {"b": Qb}, k_choices=(10,), ef_range=(16, 128), seed=8)
+    for r in rb:
+        r["t"] += 0.03  # b's burst after a's
+    done = srv.run(ra + rb, time_limit=60.0)
+    assert len(done) == len(ra) + len(rb)
+    assert srv.stats["peak_bytes"] <= max(pa, pb) * 2
+    assert srv.stats["admissions_waited_for_memory"] > 0 and srv.stats["pages_released"] > 0
+    for r in done[::11]:
+        si, sd = single(idx_a if r["index"] == "a" else idx_b, r["query"], r["k"], r["ef"])
+        assert np.array_equal(si, r["ids"]) and np.array_equal(sd, r["dists"])
+    assert S.status_counts(done)["bad_id"] == 0
 
 
 def test_autotuner_returns_result_preserving_settings(two_indices, tmp_path):
@@ -126,11 +151,14 @@ def test_admission_bytes_follow_the_settings(two_indices):
     assert K.kann_search_workspace_bytes(idx_a, 10, 10, K.KANN_MAX_EF + 1) == 0
     assert K.kann_search_workspace_bytes(idx_a, 10, 0, 64) == 0
     assert K.kann_search_workspace_bytes(idx_a, -1, 10, 64) == 0
-    # the server sizes its slots with it, halving the capacity until they fit the budget
+    # the server sizes its pages with it, halving the capacity until one fits
+    # the budget, and never lets the live pages exceed the budget
     spec = {"a": dict(index=idx_a, d=128, kmax=10, efmax=64)}
-    per_slot = K.kann_search_workspace_bytes(idx_a, 64, 10, 64)
-    srv = S.SearchServer(spec, slots_per_index=2, slot_capacity=256, memory_budget=2 * per_slot)
-    assert srv.device_bytes == 2 * per_slot
-    assert all(s.cap == 64 for s in srv.slots["a"])
+    per_page = K.kann_search_workspace_bytes(idx_a, 64, 10, 64)
+    srv = S.SearchServer(spec, page_capacity=256, memory_budget=per_page)
+    assert srv.caps["a"] == 64 and srv.page_bytes["a"] == per_page
+    reqs = S.poisson_requests(100000.0, 0.01, {"a": Qa}, k_choices=(10,), ef_range=(16, 64), seed=2)
+    done = srv.run(reqs, time_limit=60.0)
+    assert len(done) == len(reqs) and srv.stats["peak_bytes"] <= per_page and len(srv.pages) == 1
     with pytest.raises(ValueError):
         S.SearchServer({"a": dict(index=idx_a, d=128, kmax=10, efmax=K.KANN_MAX_EF + 1)})

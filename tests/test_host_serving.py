@@ -32,3 +32,11 @@ def test_latency_summary():
     assert s["completed"] == 100 and s["qps"] == 50.0
     assert abs(s["p50_ms"] - 50.5) < 1e-9 and abs(s["p99_ms"] - 99.01) < 1e-9
     assert S.latency_summary([], 1.0) == {"completed": 0}
+
+
+def test_status_counts():
+    from paper_2501_06121_b300 import kann as K
+    done = [{"status": 0}, {"status": K.KANN_QSTAT_HOPCAP | K.KANN_QSTAT_FORGOT}, {"status": K.KANN_QSTAT_FORGOT},
+            {}]
+    c = S.status_counts(done)
+    assert c == {"hop_cap": 1, "forgot": 2, "bad_id": 0, "query_truncated": 0}

@@ -12,8 +12,8 @@ Admission is by device memory: every page counts the bytes
 pages alive at any time never exceed the memory budget.  When requests of an
 index are waiting and no page of that index is idle, the server creates one if
 the budget has room, else releases the least recently used idle page of
-another index and takes its memory, else the requests wait until a running
-batch finishes and frees its page.  So arriving requests are admitted as
+another index that has no requests waiting and takes its memory, else the
+requests wait until a running batch finishes and frees its page.  So arriving requests are admitted as
 memory (not a fixed partition of it) frees up, batches of different indices
 overlap on the device on their own streams, and a burst on one index can use
 the memory that idle indices are not using.  Every finished request carries
@@ -155,17 +155,21 @@ class SearchServer:
         self.stats["peak_bytes"] = max(self.stats["peak_bytes"], self.live_bytes())
         return p
 
-    def _page_for(self, name):
+    def _page_for(self, name, pending):
         """An idle page of index `name`, made room for within the budget, or
-        None when the memory is taken by running batches."""
+        None when the memory is taken by running batches and by pages of
+        indices that have requests waiting."""
         for p in self.pages:
             if p.name == name and p.busy is None:
                 return p
         need = self.page_bytes[name]
         if self.live_bytes() + need <= self.budget and len(self.pages) < self.max_pages:
             return self._new_page(name)
-        # release idle pages of other indices, least recently used first
-        idle = sorted((p for p in self.pages if p.busy is None and p.name != name), key=lambda p: p.last_used)
+        # release idle pages of other indices that have nothing waiting, least
+        # recently used first (a page of an index with waiting requests is
+        # about to be used again: taking it would only trade captures)
+        idle = sorted((p for p in self.pages if p.busy is None and p.name != name and not pending[p.name]),
+                      key=lambda p: p.last_used)
         for p in idle:
             if self.live_bytes() + need <= self.budget and len(self.pages) < self.max_pages:
                 break
@@ -216,7 +220,7 @@ class SearchServer:
             for _, name in order:
                 q = pending[name]
                 while q:
-                    page = self._page_for(name)
+                    page = self._page_for(name, pending)
                     if page is None:
                         if id(q[0]) not in waited:
                             waited.add(id(q[0]))

@@ -316,7 +316,7 @@ def run_reference(args):
     print(json.dumps(out))
 
 
-def run_serving(g, Xd, Q, dev, args):
+def run_serving(dev, args):
     """Continuous-batching serving of two resident indices: the 10k x 128
     Gaussian mixture (32 clusters, sigma 5; M=16, efC=100) and a 768-d index
     (`--serving-768-n` unit vectors, inner product, the concentrated mixture
@@ -617,7 +617,7 @@ def main():
     ap.add_argument("--serving-pq", action="store_true", help="also serve the 768-d index with PQ codes")
     ap.add_argument("--serving-memory", type=int, default=48 << 20)
     ap.add_argument("--serving-rates", default="5000,20000,50000,100000,200000")
-    ap.add_argument("--workload", default="sift1m", choices=["sift1m", "pq768", "sparse", "sparse100k"])
+    ap.add_argument("--workload", default="sift1m", choices=["sift1m", "pq768", "sparse", "sparse100k", "serving"])
     ap.add_argument("--sparse-n", type=int, default=1_000_000)
     ap.add_argument("--sparse-host-build", action="store_true")
     ap.add_argument("--pq-n", type=int, default=1_000_000)
@@ -632,6 +632,12 @@ def main():
         return run_sparse(args, n_docs=100_000)
     if args.workload == "sparse":
         return run_sparse(args)
+    if args.workload == "serving":
+        import torch
+        from paper_2501_06121_b300 import build as lib_build
+        lib_build.build()
+        print(json.dumps({"workload": "serving", "serving": run_serving(torch.device("cuda", 0), args)}))
+        return None
 
     import torch
     import torch.distributed as dist
@@ -875,7 +881,7 @@ def main():
 
     serving = None
     if rank == 0 and world == 1 and not args.no_serving:
-        serving = run_serving(g, Xd, Q, dev, args)
+        serving = run_serving(dev, args)
 
     cpu_base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -322,15 +322,19 @@ int kann_quantize(const float* d_x, int64_t n, int d, int dtype, void* d_out, fl
 
 /* ---- PQ codebooks (device) -------------------------------------------------
  * Product Quantization (Sec. 2, citing Jegou et al.) as index preparation:
- * kann_pq_train runs `iters` Lloyd iterations per subspace (m subspaces of
- * dsub = d / m <= 16 dims, 256 centroids each) on FP32 rows d_x [n][d]
- * (n >= 256), starting from 256 distinct training rows per subspace drawn by
- * a counter-based SplitMix64 keyed by (seed, subspace, draw); a centroid
- * that loses all its points keeps its position.  Writes d_codebooks
- * [m][256][dsub]; d_ws is caller scratch of kann_pq_train_workspace_bytes.
- * kann_pq_encode writes d_codes [n][m]: nearest centroid per subspace under
- * L2 in FP32, ties to the lowest index.  Both are asynchronous on `stream`. */
-size_t kann_pq_train_workspace_bytes(int d, int m);
+ * kann_pq_train trains 256 centroids per subspace (m subspaces of
+ * dsub = d / m <= 16 dims) on FP32 rows d_x [n][d] (n >= 256): k-means++
+ * seeding (centroid c drawn with the counter-based SplitMix64 uniform keyed by
+ * (seed ^ (j + 1) * 0xD1B54A32D192ED03, c), the first row whose running sum of
+ * squared distances to the nearest centroid so far reaches u * the total),
+ * then `iters` Lloyd iterations (nearest centroid, strictly smaller wins;
+ * means; an empty centroid moves to the farthest row), all in FP64 -- the
+ * steps of the oracle's reading, equal to it bit for bit on integer data.
+ * Writes d_codebooks [m][256][dsub] (FP32, rounded from FP64); d_ws is
+ * caller scratch of kann_pq_train_workspace_bytes(n, d, m).  kann_pq_encode
+ * writes d_codes [n][m]: nearest centroid per subspace under L2 in FP32, ties
+ * to the lowest index.  Both are asynchronous on `stream`. */
+size_t kann_pq_train_workspace_bytes(int64_t n, int d, int m);
 int kann_pq_train(const float* d_x, int64_t n, int d, int m, int iters, uint64_t seed, float* d_codebooks, void* d_ws,
                   size_t ws_bytes, void* stream);
 int kann_pq_encode(const float* d_x, int64_t n, int d, int m, const float* d_codebooks, uint8_t* d_codes,

@@ -94,7 +94,7 @@ def _lib():
             "kann_hnsw_build_dense": (I, [P, I64, I, I, I, I, U64, I, P, P, P, P, P]),
             "kann_hnsw_build_sparse": (I, [P, P, P, I64, I, I, U64, I, P, P, P, P, P]),
             "kann_exact_knn_sparse": (I, [P, P, P, I64, P, P, P, I, I, I, P, P, P]),
-            "kann_pq_train_workspace_bytes": (SZ, [I, I]),
+            "kann_pq_train_workspace_bytes": (SZ, [I64, I, I]),
             "kann_pq_train": (I, [P, I64, I, I, I, U64, P, P, SZ, P]),
             "kann_pq_encode": (I, [P, I64, I, I, P, P, P]),
             "kann_hnsw_build_device_workspace_bytes": (SZ, [I64, I, I, I, I]),
@@ -372,7 +372,7 @@ def kann_pq_train(x, m, iters=25, seed=0, stream=None):
     _require_cuda(x)
     n, d = x.shape
     cb = torch.empty((m, 256, d // m), dtype=torch.float32, device=x.device)
-    wsb = int(_lib().kann_pq_train_workspace_bytes(d, m))
+    wsb = int(_lib().kann_pq_train_workspace_bytes(n, d, m))
     ws = torch.empty(max(wsb, 16), dtype=torch.uint8, device=x.device)
     _check("kann_pq_train", _lib().kann_pq_train(_dev(x), n, d, m, iters, seed, _dev(cb), _dev(ws), ws.numel(),
                                                  _stream(stream)))

@@ -573,6 +573,74 @@ def run_sparse(args, n_docs=None):
                       "ground_truth_s_1000q": gt_s, "rows": rows}))
 
 
+def run_big(args):
+    """The MS MARCO Star/Dragon-sized stand-in (Sec. 3, Table 1: 8,841,823
+    passages, 768-d, inner product): `--big-n` unit vectors of the
+    concentrated mixture normalize(mu + 0.04 g) over 1,024 directions,
+    generated block by block straight to the device, 10k queries; HNSW M=32,
+    efC=200 built with the layer-0 insertions on the GPU; PQ m=192 trained on
+    the GPU on 100k rows, searched with the uint8 table and an FP32 re-rank of
+    the best 100, beside plain FP32 traversal; ground truth: exact FP32 k-NN of
+    the first 1,000 queries."""
+    import torch
+    from paper_2501_06121_b300 import build as lib_build
+    from paper_2501_06121_b300 import datagen as G
+    from paper_2501_06121_b300 import kann as K_
+    lib_build.build()
+    dev = torch.device("cuda", 0)
+    n, d = args.big_n, 768
+    t0 = time.time()
+    blocks, Q = G.vmf_mixture_blocks(n, 10_000, d=d, clusters=1024, kappa=50.0, seed=3, concentration=0.04)
+    Xd = torch.empty((n, d), dtype=torch.float32, device=dev)
+    for s0, blk in blocks:
+        Xd[s0:s0 + len(blk)].copy_(torch.from_numpy(blk))
+    torch.cuda.synchronize()
+    gen_s = time.time() - t0
+    t0 = time.time()
+    g = K_.kann_hnsw_build_device(Xd, K_.KANN_IP, 32, 200, 3)
+    build_s = time.time() - t0
+    t0 = time.time()
+    cb = K_.kann_pq_train(Xd[:100_000].contiguous(), 192, iters=25, seed=3)
+    codes = K_.kann_pq_encode(Xd, cb)
+    torch.cuda.synchronize()
+    pq_s = time.time() - t0
+    gd = K_.graph_to_device(g, dev)
+    del g
+    Qd = torch.from_numpy(Q).to(dev)
+    idx_pq = K_.kann_index_upload(gd, pq=dict(codes=codes, codebooks=cb, metric=K_.KANN_IP), rerank=Xd)
+    idx32 = K_.kann_index_upload(gd, vectors=Xd, dtype=K_.KANN_F32, metric=K_.KANN_IP)
+    ngt = 1000
+    t0 = time.time()
+    gt, _ = K_.kann_exact_knn(Qd[:ngt].contiguous(), Xd, 10, K_.KANN_IP)
+    torch.cuda.synchronize()
+    gt_s = time.time() - t0
+    gt = gt.cpu().numpy()
+
+    def timed(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+        e0.record()
+        for _ in range(reps):
+            out = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / reps, out
+
+    rows = []
+    for ef in (16, 32, 48, 64, 128, 256):
+        ms8, (i8, _) = timed(lambda: K_.kann_search_ex(idx_pq, Qd, 10, ef, rerank=100, pq_lut=K_.KANN_PQ_LUT_U8))
+        ms32, (i32, _) = timed(lambda: K_.kann_search_ex(idx32, Qd, 10, ef))
+        rows.append({"ef": ef, "pq_u8table_rerank100_qps": 1e4 / (ms8 / 1e3),
+                     "pq_u8table_rerank100_recall": recall_at(i8.cpu().numpy()[:ngt], gt),
+                     "fp32_qps": 1e4 / (ms32 / 1e3), "fp32_recall": recall_at(i32.cpu().numpy()[:ngt], gt)})
+        print(json.dumps(rows[-1]), flush=True)
+    dev_bytes = {"fp32_rows": n * d * 4, "pq_codes": n * 192, "graph_layer0": n * 64 * 4}
+    print(json.dumps({"workload": "msmarco_dense", "n": n, "d": d, "data_gen_s": gen_s, "graph_build_s": build_s,
+                      "graph_builder": "device", "pq_train_encode_s": pq_s, "ground_truth_s_1000q": gt_s,
+                      "device_bytes": dev_bytes, "rows": rows}))
+
+
 SEARCH_KERNEL_SOURCES = ("kann_device.cuh", "kann_internal.h", "kann_search_impl.cuh", "kann_search_f16.cu")
 
 
@@ -617,7 +685,9 @@ def main():
     ap.add_argument("--serving-pq", action="store_true", help="also serve the 768-d index with PQ codes")
     ap.add_argument("--serving-memory", type=int, default=48 << 20)
     ap.add_argument("--serving-rates", default="5000,20000,50000,100000,200000")
-    ap.add_argument("--workload", default="sift1m", choices=["sift1m", "pq768", "sparse", "sparse100k", "serving"])
+    ap.add_argument("--workload", default="sift1m",
+                    choices=["sift1m", "pq768", "sparse", "sparse100k", "serving", "msmarco_dense"])
+    ap.add_argument("--big-n", type=int, default=8_841_823)
     ap.add_argument("--sparse-n", type=int, default=1_000_000)
     ap.add_argument("--sparse-host-build", action="store_true")
     ap.add_argument("--pq-n", type=int, default=1_000_000)
@@ -632,6 +702,8 @@ def main():
         return run_sparse(args, n_docs=100_000)
     if args.workload == "sparse":
         return run_sparse(args)
+    if args.workload == "msmarco_dense":
+        return run_big(args)
     if args.workload == "serving":
         import torch
         from paper_2501_06121_b300 import build as lib_build

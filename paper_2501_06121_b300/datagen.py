@@ -89,6 +89,25 @@ def _wood_w(rng, m, d, kappa):
     return out
 
 
+def _vmf_blocks(rng, m, d, mus, kappa, concentration):
+    """Rows of the von Mises-Fisher mixture (or the concentrated variant) in
+    blocks of 32,768: yields (first row, float32 block)."""
+    step = 1 << 15
+    clusters = len(mus)
+    for s in range(0, m, step):
+        e = min(m, s + step)
+        mu = mus[_pick(rng, e - s, clusters)]
+        if concentration is not None:
+            v = mu + concentration * rng.standard_normal((e - s, d))
+            yield s, (v / np.linalg.norm(v, axis=1, keepdims=True)).astype(np.float32)
+            continue
+        w = _wood_w(rng, e - s, d, kappa)
+        g = rng.standard_normal((e - s, d))
+        g -= np.sum(g * mu, axis=1, keepdims=True) * mu
+        g /= np.linalg.norm(g, axis=1, keepdims=True)
+        yield s, (w[:, None] * mu + np.sqrt(np.maximum(0.0, 1.0 - w * w))[:, None] * g).astype(np.float32)
+
+
 def vmf_mixture(n, nq, d=768, clusters=1024, kappa=50.0, seed=3, concentration=None):
     """Unit-norm mixture of von Mises-Fisher components (Wood's sampler),
     uniform component choice, mean directions uniform on the sphere.  With
@@ -98,22 +117,22 @@ def vmf_mixture(n, nq, d=768, clusters=1024, kappa=50.0, seed=3, concentration=N
 
     def draw(rng, m):
         out = np.empty((m, d), np.float32)
-        step = 1 << 15
-        for s in range(0, m, step):
-            e = min(m, s + step)
-            mu = mus[_pick(rng, e - s, clusters)]
-            if concentration is not None:
-                v = mu + concentration * rng.standard_normal((e - s, d))
-                out[s:e] = v / np.linalg.norm(v, axis=1, keepdims=True)
-                continue
-            w = _wood_w(rng, e - s, d, kappa)
-            g = rng.standard_normal((e - s, d))
-            g -= np.sum(g * mu, axis=1, keepdims=True) * mu
-            g /= np.linalg.norm(g, axis=1, keepdims=True)
-            out[s:e] = w[:, None] * mu + np.sqrt(np.maximum(0.0, 1.0 - w * w))[:, None] * g
+        for s, blk in _vmf_blocks(rng, m, d, mus, kappa, concentration):
+            out[s:s + len(blk)] = blk
         return out
 
     return draw(rb, n), draw(rq, nq)
+
+
+def vmf_mixture_blocks(n, nq, d=768, clusters=1024, kappa=50.0, seed=3, concentration=None):
+    """The rows of vmf_mixture(n, nq, ...) without holding the base set:
+    (a generator of (first row, block) over the n base rows, the queries)."""
+    rb, rq, rp = _streams(seed)
+    mus = _unit(rp, clusters, d)
+    queries = np.empty((nq, d), np.float32)
+    for s, blk in _vmf_blocks(rq, nq, d, mus, kappa, concentration):
+        queries[s:s + len(blk)] = blk
+    return _vmf_blocks(rb, n, d, mus, kappa, concentration), queries
 
 
 def _zipf_cdf(vocab, s):

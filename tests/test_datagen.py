@@ -43,3 +43,12 @@ def test_sparse_law():
     assert cnt.argmax() == 0
     assert np.all(w > 0)
     assert abs(np.diff(qs[0]).mean() - 40) < 2.0
+
+
+def test_vmf_blocks_are_the_rows_of_the_whole_draw():
+    from paper_2501_06121_b300 import datagen as G
+    for conc in (None, 0.04):
+        X, Q = G.vmf_mixture(70000, 50, d=16, clusters=8, seed=9, concentration=conc)
+        blocks, Qb = G.vmf_mixture_blocks(70000, 50, d=16, clusters=8, seed=9, concentration=conc)
+        Xb = np.concatenate([b for _, b in blocks])
+        assert np.array_equal(X, Xb) and np.array_equal(Q, Qb)

@@ -545,32 +545,58 @@ def run_sparse(args, n_docs=None):
     hbm = peaks.get("hbm_gbs", 6400.0)
     from paper_2501_06121_b300 import autotune as A_
     rows = []
+    # the search sweep in an NVTX range named "search", so that a profiler
+    # can take its launches apart from the graph build's
+    torch.cuda.nvtx.range_push("search")
     for ef in (32, 64, 128, 256, 512, 1024):
         cnt = torch.zeros((len(qs[0]) - 1, 4), dtype=torch.int32, device=dev)
         K_.kann_search_sparse(idx, q_d[0], q_d[1], q_d[2], 10, ef, counters=cnt, hash_bits=15)
         torch.cuda.synchronize()
         c = cnt.double().mean(0).cpu().numpy()
         bq = c[0] * doc_bytes + c[1] * 64 * 4 + c[2] * doc_bytes + c[3] * 32 * 4 + q_bytes + 10 * 8
-        opts = dict(hash_bits=12 if ef <= 256 else 13)
-        run = lambda: K_.kann_search_sparse(idx, q_d[0], q_d[1], q_d[2], 10, ef, **opts)
-        run()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
-        e0.record()
-        for _ in range(5):
-            ids, _ = run()
-        e1.record()
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / 5
+        # launch settings (visited table size, team size) by timing; every
+        # one returns the same results, which is checked
+        opts, ms, (ids, _) = fastest(lambda **o: K_.kann_search_sparse(idx, q_d[0], q_d[1], q_d[2], 10, ef, **o),
+                                     [dict(hash_bits=hb, team=t) for hb in (12, 13, 14) for t in (0, 2, 4)])
         rows.append({"ef": ef, "qps": 1e4 / (ms / 1e3), "ms": ms,
                      "recall@10": recall_at(ids.cpu().numpy()[:ngt], gt, 10),
                      "docs_evaluated_per_query": c[0] + c[2], "algorithmic_bytes_per_query": bq,
                      "roofline_frac": 1e4 * bq / (ms / 1e3) / 1e9 / hbm, "launch": opts})
         print(json.dumps(rows[-1]), flush=True)
+    torch.cuda.nvtx.range_pop()
     print(json.dumps({"workload": "sparse", "docs": n_docs, "data_gen_s": gen_s, "graph_build_s": build_s,
                       "graph_builder": "host" if args.sparse_host_build else "device",
                       "doc_bytes_indegree_weighted": doc_bytes, "peak_gbs": hbm,
                       "ground_truth_s_1000q": gt_s, "rows": rows}))
+
+
+def fastest(run, options, reps=3):
+    """Times run(**o) for each option dict (CUDA events, after one untimed
+    call) and returns (option, ms, output) of the fastest whose output equals
+    the first option's bit for bit (launch settings never change results;
+    one that did would be a fault, and is not chosen)."""
+    import torch
+    best = None
+    ref = None
+    for o in options:
+        try:
+            out = run(**o)
+        except RuntimeError:
+            continue
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+        e0.record()
+        for _ in range(reps):
+            out = run(**o)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        if ref is None:
+            ref = out
+        same = all(torch.equal(a, b) for a, b in zip(out, ref))
+        if same and (best is None or ms < best[1]):
+            best = (dict(o), ms, out)
+    return best
 
 
 def run_big(args):
@@ -609,6 +635,10 @@ def run_big(args):
     Qd = torch.from_numpy(Q).to(dev)
     idx_pq = K_.kann_index_upload(gd, pq=dict(codes=codes, codebooks=cb, metric=K_.KANN_IP), rerank=Xd)
     idx32 = K_.kann_index_upload(gd, vectors=Xd, dtype=K_.KANN_F32, metric=K_.KANN_IP)
+    # the BF16 re-rank copy (half the re-rank bytes; its distances are FP32
+    # arithmetic on BF16-rounded rows)
+    Xb, _ = K_.kann_quantize(Xd, K_.KANN_BF16)
+    idx_pqb = K_.kann_index_upload(gd, pq=dict(codes=codes, codebooks=cb, metric=K_.KANN_IP), rerank=Xb)
     ngt = 1000
     t0 = time.time()
     gt, _ = K_.kann_exact_knn(Qd[:ngt].contiguous(), Xd, 10, K_.KANN_IP)
@@ -628,14 +658,22 @@ def run_big(args):
         return e0.elapsed_time(e1) / reps, out
 
     rows = []
+    torch.cuda.nvtx.range_push("search")  # the sweep, apart from the build (for a profiler)
     for ef in (16, 32, 48, 64, 128, 256):
         ms8, (i8, _) = timed(lambda: K_.kann_search_ex(idx_pq, Qd, 10, ef, rerank=100, pq_lut=K_.KANN_PQ_LUT_U8))
-        ms32, (i32, _) = timed(lambda: K_.kann_search_ex(idx32, Qd, 10, ef))
+        msb, (ib, _) = timed(lambda: K_.kann_search_ex(idx_pqb, Qd, 10, ef, rerank=100, pq_lut=K_.KANN_PQ_LUT_U8))
+        o32, ms32, (i32, _) = fastest(lambda **o: K_.kann_search_ex(idx32, Qd, 10, ef, **o),
+                                      [dict(team=t, hash_bits=hb) for t in (0, 2, 4) for hb in (0, 13)])
         rows.append({"ef": ef, "pq_u8table_rerank100_qps": 1e4 / (ms8 / 1e3),
                      "pq_u8table_rerank100_recall": recall_at(i8.cpu().numpy()[:ngt], gt),
-                     "fp32_qps": 1e4 / (ms32 / 1e3), "fp32_recall": recall_at(i32.cpu().numpy()[:ngt], gt)})
+                     "pq_u8table_bf16rerank100_qps": 1e4 / (msb / 1e3),
+                     "pq_u8table_bf16rerank100_recall": recall_at(ib.cpu().numpy()[:ngt], gt),
+                     "fp32_qps": 1e4 / (ms32 / 1e3), "fp32_recall": recall_at(i32.cpu().numpy()[:ngt], gt),
+                     "fp32_launch": o32})
         print(json.dumps(rows[-1]), flush=True)
-    dev_bytes = {"fp32_rows": n * d * 4, "pq_codes": n * 192, "graph_layer0": n * 64 * 4}
+    torch.cuda.nvtx.range_pop()
+    dev_bytes = {"fp32_rows": n * d * 4, "bf16_rerank_rows": n * d * 2, "pq_codes": n * 192,
+                 "graph_layer0": n * 64 * 4}
     print(json.dumps({"workload": "msmarco_dense", "n": n, "d": d, "data_gen_s": gen_s, "graph_build_s": build_s,
                       "graph_builder": "device", "pq_train_encode_s": pq_s, "ground_truth_s_1000q": gt_s,
                       "device_bytes": dev_bytes, "rows": rows}))

@@ -177,7 +177,7 @@ typedef struct {
                               KANN_PQ_LUT_U8 (2): uint8 values v = rint(clamp((entry - min_j) /
                               scale, 0, 255)), min_j the minimum of subspace j, scale = (largest
                               max_j - min_j) / 255, entries in FP32: a quarter of the shared
-                              memory (three queries per SM at m = 192).  Rows are ordered by the
+                              memory (four queries per SM at m = 192).  Rows are ordered by the
                               exact integer sum of their values; the distance reported (without
                               re-rank) is sum_j min_j + scale * sum (two FP32 roundings). */
   uint32_t* d_status;      /* [n] per-query KANN_QSTAT_* bits, nullable */
@@ -207,6 +207,15 @@ typedef struct {
                               flight per dependent step; its results are defined by that rule,
                               not by the one-expansion search.  PQ and sparse indices: KANN_EINVAL
                               unless 0 or 1.  max_hops counts expansions */
+  int32_t team;            /* dense and sparse indices: warps sharing one query.  0 or 1 = one
+                              warp per query (warps_per_block of them per CTA); 2 or 4 = one
+                              query per CTA of that many warps: warp 0 runs the search and at
+                              every distance and re-rank batch each warp evaluates one slice
+                              of the candidates, every row by one lane group as in the one-warp
+                              search, so results are identical bit for bit (more warps per SM
+                              when each query's shared memory limits them; warps_per_block is
+                              then ignored).  PQ indices always run teams of 8 warps and take
+                              0 only; with expand > 1: KANN_EINVAL unless 0 or 1 */
 } kann_search_opts;
 
 /* HNSW K-NN-SEARCH (Malkov & Yashunin Alg. 5) for n dense FP32 queries

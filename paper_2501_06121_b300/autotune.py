@@ -2,8 +2,8 @@
 
 The settings that do not change results -- lanes per row gather, the
 visited table's layout (compact 16-bit or wide 32-bit slots) and size,
-warps per CTA, the lean register budget, plain vs persistent work-stealing
-launch -- are timed on the caller's queries with CUDA events; a setting is
+warps per CTA, the team size (warps sharing one query), the lean register
+budget, plain vs persistent work-stealing launch -- are timed on the caller's queries with CUDA events; a setting is
 accepted only if it returns exactly the same ids and distances as the
 default launch (they all must: the search is defined by (k, ef) alone).
 The table size trades shared memory (hence queries resident per SM) against
@@ -44,7 +44,7 @@ def _time(index, Q, k, ef, reps, opts):
 def tune(index, queries, k, ef, rerank=0, reps=5, cache_path=None, verbose=False):
     """Returns the fastest result-preserving option dict for kann_search_ex
     (keys lanes_per_row, hash_bits, visited_format, warps_per_block, lean,
-    persistent)."""
+    team, persistent)."""
     key = _signature(index, k, ef, rerank)
     cache = {}
     if cache_path and os.path.exists(cache_path):
@@ -53,7 +53,8 @@ def tune(index, queries, k, ef, rerank=0, reps=5, cache_path=None, verbose=False
         if key in cache:
             return dict(cache[key]["opts"])
     base_t, (ref_i, ref_d) = _time(index, queries, k, ef, reps, dict(rerank=rerank))
-    best = dict(lanes_per_row=0, hash_bits=0, visited_format=0, warps_per_block=0, lean=0, persistent=False)
+    best = dict(lanes_per_row=0, hash_bits=0, visited_format=0, warps_per_block=0, lean=0, team=0,
+                persistent=False)
     best_t = base_t
     results = []
 
@@ -77,6 +78,11 @@ def tune(index, queries, k, ef, rerank=0, reps=5, cache_path=None, verbose=False
         for pers in (False, True):
             trial(dict(best, warps_per_block=wpb, persistent=pers))
     trial(dict(best, lean=1))
+    # teams of 2 and 4 warps per query: more warps per SM when each query's
+    # shared memory (beam, visited table) is what limits them
+    for team in (2, 4):
+        for pers in (False, True):
+            trial(dict(best, team=team, warps_per_block=0, lean=0, persistent=pers))
     # the table size again, at the chosen lane mapping and CTA shape
     for vf, hb in tables:
         trial(dict(best, visited_format=vf, hash_bits=hb))

@@ -14,7 +14,9 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 
 CU_SOURCES = ["kann_api.cu", "kann_search.cu", "kann_search_f32.cu", "kann_search_f16.cu", "kann_search_bf16.cu",
               "kann_search_e4m3.cu", "kann_search_f32_multi.cu", "kann_search_f16_multi.cu",
-              "kann_search_bf16_multi.cu", "kann_search_e4m3_multi.cu", "kann_exact.cu", "kann_exact_tc.cu",
+              "kann_search_bf16_multi.cu", "kann_search_e4m3_multi.cu", "kann_search_f32_team.cu",
+              "kann_search_f16_team.cu", "kann_search_bf16_team.cu", "kann_search_e4m3_team.cu",
+              "kann_exact.cu", "kann_exact_tc.cu",
               "kann_pq.cu", "kann_exact_sparse.cu", "kann_build_gpu.cu"]
 CPP_SOURCES = ["kann_build.cpp"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")

@@ -166,6 +166,7 @@ int fill_search_args(const kann_index_t* idx, const float* d_q, int n, int k, in
   a.out_d = d_dists;
   a.max_hops = 1000000;
   a.expand = 1;
+  a.team = 1;
   int hbits = 0;
   int vformat = 0;
   wpb = 4;
@@ -190,6 +191,8 @@ int fill_search_args(const kann_index_t* idx, const float* d_q, int n, int k, in
     vformat = opts->visited_format;
     if (opts->expand < 0 || opts->expand > KANN_MAX_EXPAND) return KANN_EINVAL;
     if (opts->expand > 1) a.expand = opts->expand;
+    if (opts->team != 0 && opts->team != 1 && opts->team != 2 && opts->team != 4) return KANN_EINVAL;
+    if (opts->team > 1) a.team = opts->team;
     R = opts->rerank;
     if (R < -1) return KANN_EINVAL;
     a.work_counter = opts->d_work_counter;
@@ -228,6 +231,7 @@ int fill_search_args(const kann_index_t* idx, const float* d_q, int n, int k, in
 int plan_shared(const kann_index_t* idx, SearchArgs& a, int& wpb) {
   const int optin = max_optin_smem();
   if (idx->kind != 0 && a.expand > 1) return KANN_EINVAL;  // multi-expansion: dense indices
+  if (a.team > 1 && (idx->kind == 1 || a.expand > 1)) return KANN_EINVAL;  // teams: dense/sparse, one expansion
   if (idx->kind == 1) {
     const int m = idx->pq.m;
     a.warp_smem = search_warp_smem_pq(a.efcap, a.hbits, a.vis_r >= 0, m, a.lut);
@@ -241,6 +245,10 @@ int plan_shared(const kann_index_t* idx, SearchArgs& a, int& wpb) {
   const bool compact = a.vis_r >= 0;
   a.warp_smem = idx->kind == 2 ? search_warp_smem_sparse(a.efcap, a.hbits, compact, idx->sp.vocab)
                                : search_warp_smem(a.efcap, a.hbits, compact, a.expand);
+  if (a.team > 1) {
+    wpb = 1;  // one query per CTA of a.team warps, its control block after the region
+    return a.warp_smem + PQ_TEAM_CTL_BYTES > optin ? KANN_ENOMEM : KANN_OK;
+  }
   while (wpb > 1 && wpb * a.warp_smem > optin) --wpb;
   return a.warp_smem > optin ? KANN_ENOMEM : KANN_OK;
 }
@@ -256,7 +264,8 @@ int run_dense(const kann_index_t* idx, SearchArgs& a, int wpb, void* stream) {
   a.lpr = a.lpr_override ? a.lpr_override : lanes_per_row(a.nchunks, default_chunks_per_lane(v.dtype));
   if (a.lpr > a.nchunks && a.nchunks >= 1) a.lpr = lanes_per_row(a.nchunks);
   if ((a.nchunks + a.lpr - 1) / a.lpr > 8) return KANN_EINVAL;
-  if ((a.nchunks + a.lpr - 1) / a.lpr != 2 || a.expand > 1) a.lean = 0;  // lean: 2 chunks per lane, one expansion
+  // lean: 2 chunks per lane, one expansion, one warp per query
+  if ((a.nchunks + a.lpr - 1) / a.lpr != 2 || a.expand > 1 || a.team > 1) a.lean = 0;
   if (a.nq > 0 && (!a.q || !aligned16(a.q))) return KANN_EINVAL;
   const int rc = plan_shared(idx, a, wpb);
   if (rc != KANN_OK || a.nq == 0) return rc;

@@ -49,7 +49,8 @@ struct SearchArgs {
   int lut;               // PQ: per-query table format (KANN_PQ_LUT_F32 / F16 / U8)
   int efcap;       // W capacity (efmax rounded up to a multiple of 32)
   int expand;      // layer-0 entries expanded per step (1 = the HNSW step; 2..KANN_MAX_EXPAND: batched)
-  int warp_smem;   // bytes of shared memory per warp
+  int team;        // dense/sparse: warps per query (1 = one warp per query; 2 or 4 = a CTA per query)
+  int warp_smem;   // bytes of shared memory per warp (per query region of a team)
 };
 
 // Sparse search additions.
@@ -83,6 +84,12 @@ SearchKernelFn pick_search_f32_multi(int cplt, int metric, int lpr_exact);
 SearchKernelFn pick_search_f16_multi(int cplt, int metric, int lpr_exact);
 SearchKernelFn pick_search_bf16_multi(int cplt, int metric, int lpr_exact);
 SearchKernelFn pick_search_e4m3_multi(int cplt, int metric, int lpr_exact);
+// Team kernels (a CTA of `team` = 2 or 4 warps per query), compiled in
+// kann_search_{f32,f16,bf16,e4m3}_team.cu.
+SearchKernelFn pick_search_f32_team(int cplt, int metric, int lpr_exact, int team);
+SearchKernelFn pick_search_f16_team(int cplt, int metric, int lpr_exact, int team);
+SearchKernelFn pick_search_bf16_team(int cplt, int metric, int lpr_exact, int team);
+SearchKernelFn pick_search_e4m3_team(int cplt, int metric, int lpr_exact, int team);
 
 // Candidate keys a warp keeps per step: 64 per expanded entry, plus 64 for
 // the ranked survivors of a batch when several entries are expanded at once.
@@ -92,7 +99,7 @@ __host__ __device__ constexpr int cand_keys(int expand) { return 64 * expand + (
 // (compact: a visited table of 16-bit slots, else 32-bit).
 int search_warp_smem(int efcap, int hbits, bool compact, int expand = 1);
 int search_warp_smem_pq(int efcap, int hbits, bool compact, int m, int lut = KANN_PQ_LUT_F32);
-// Shared memory of a PQ search team's control block (after the query's region).
+// Shared memory of a search team's control block (after the query's region).
 constexpr int PQ_TEAM_CTL_BYTES = 64;
 int search_warp_smem_sparse(int efcap, int hbits, bool compact, int vocab);
 

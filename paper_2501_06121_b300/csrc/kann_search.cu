@@ -12,16 +12,26 @@ __global__ void __launch_bounds__(128, 4) search_sparse_kernel(const SearchArgs 
   run_queries(a, be);
 }
 
-// Grid of a launch: one warp per query, or (persistent) as many CTAs as fit
-// on the GPU at once.
+// A team kernel of the sparse back-end: one query per CTA of T warps.
+template <int T>
+__global__ void __launch_bounds__(T * 32, 16 / T)
+    search_sparse_team_kernel(const SearchArgs a, const __grid_constant__ SparseArgs sp) {
+  SparseBackend be;
+  be.sp = &sp;
+  run_queries_team<T>(a, be);
+}
+
+// Grid of a launch of CTAs of `warps` warps, `per_cta` queries each: one
+// CTA per per_cta queries, or (persistent) as many CTAs as fit on the GPU at
+// once.
 template <class F>
-int launch_grid(F fn, const SearchArgs& a, int wpb, size_t smem) {
-  const int plain = (a.nq + wpb - 1) / wpb;
+int launch_grid(F fn, const SearchArgs& a, int warps, int per_cta, size_t smem) {
+  const int plain = (a.nq + per_cta - 1) / per_cta;
   if (a.work_counter == nullptr) return plain;
   int dev = 0, sms = 148, per_sm = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, wpb * 32, smem) != cudaSuccess || per_sm < 1)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, warps * 32, smem) != cudaSuccess || per_sm < 1)
     per_sm = 1;
   const int full = sms * per_sm;
   return plain < full ? plain : full;
@@ -55,6 +65,26 @@ int launch_search_dense(const SearchArgs& a, int dtype, int wpb, void* stream) {
   const int cplt = pow2_at_least((a.nchunks + a.lpr - 1) / a.lpr);
   const int lpr_exact = a.nchunks == a.lpr * cplt ? a.lpr : 0;
   SearchKernelFn fn = nullptr;
+  if (a.team > 1) {
+    // one query per CTA of a.team warps, the team's control block after the
+    // query's region
+    switch (dtype) {
+      case KANN_F32: fn = pick_search_f32_team(cplt, a.metric, lpr_exact, a.team); break;
+      case KANN_F16: fn = pick_search_f16_team(cplt, a.metric, lpr_exact, a.team); break;
+      case KANN_BF16: fn = pick_search_bf16_team(cplt, a.metric, lpr_exact, a.team); break;
+      case KANN_E4M3: fn = pick_search_e4m3_team(cplt, a.metric, lpr_exact, a.team); break;
+      default: break;
+    }
+    if (!fn || a.expand > 1) return (int)cudaErrorInvalidValue;
+    const size_t smem = (size_t)a.warp_smem + PQ_TEAM_CTL_BYTES;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return (int)e;
+    const int grid = launch_grid(fn, a, a.team, 1, smem);
+    int c = start_counter(a, (cudaStream_t)stream);
+    if (c) return c;
+    fn<<<grid, a.team * 32, smem, (cudaStream_t)stream>>>(a);
+    return (int)cudaGetLastError();
+  }
   switch (dtype) {
     case KANN_F32:
       fn = a.expand > 1 ? pick_search_f32_multi(cplt, a.metric, lpr_exact) : pick_search_f32(cplt, a.lean, a.metric, lpr_exact);
@@ -76,7 +106,7 @@ int launch_search_dense(const SearchArgs& a, int dtype, int wpb, void* stream) {
   const size_t smem = (size_t)wpb * a.warp_smem;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return (int)e;
-  const int grid = launch_grid(fn, a, wpb, smem);
+  const int grid = launch_grid(fn, a, wpb, wpb, smem);
   int c = start_counter(a, (cudaStream_t)stream);
   if (c) return c;
   fn<<<grid, wpb * 32, smem, (cudaStream_t)stream>>>(a);
@@ -117,15 +147,7 @@ int launch_search_pq(const SearchArgs& a, int wpb, void* stream) {
   const size_t smem = (size_t)a.warp_smem + PQ_TEAM_CTL_BYTES;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return (int)e;
-  int grid = a.nq;
-  if (a.work_counter != nullptr) {
-    int dev = 0, sms = 148, per_sm = 1;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, PQ_TEAM * 32, smem) != cudaSuccess || per_sm < 1)
-      per_sm = 1;
-    grid = a.nq < sms * per_sm ? a.nq : sms * per_sm;
-  }
+  const int grid = launch_grid(fn, a, PQ_TEAM, 1, smem);
   int c = start_counter(a, (cudaStream_t)stream);
   if (c) return c;
   fn<<<grid, PQ_TEAM * 32, smem, (cudaStream_t)stream>>>(a);
@@ -135,10 +157,23 @@ int launch_search_pq(const SearchArgs& a, int wpb, void* stream) {
 int launch_search_sparse(const SearchArgs& a, const SparseArgs& sp, int wpb, void* stream) {
   if (a.nq == 0) return 0;
   if (a.warp_smem % 16 != 0) return (int)cudaErrorInvalidValue;  // regions must stay 16-byte aligned
+  if (a.team > 1) {
+    void (*fn)(const SearchArgs, const SparseArgs) =
+        a.team == 2 ? search_sparse_team_kernel<2> : (a.team == 4 ? search_sparse_team_kernel<4> : nullptr);
+    if (!fn) return (int)cudaErrorInvalidValue;
+    const size_t smem = (size_t)a.warp_smem + PQ_TEAM_CTL_BYTES;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return (int)e;
+    const int grid = launch_grid(fn, a, a.team, 1, smem);
+    int c = start_counter(a, (cudaStream_t)stream);
+    if (c) return c;
+    fn<<<grid, a.team * 32, smem, (cudaStream_t)stream>>>(a, sp);
+    return (int)cudaGetLastError();
+  }
   const size_t smem = (size_t)wpb * a.warp_smem;
   cudaError_t e = cudaFuncSetAttribute(search_sparse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return (int)e;
-  const int grid = launch_grid(search_sparse_kernel, a, wpb, smem);
+  const int grid = launch_grid(search_sparse_kernel, a, wpb, wpb, smem);
   int c = start_counter(a, (cudaStream_t)stream);
   if (c) return c;
   search_sparse_kernel<<<grid, wpb * 32, smem, (cudaStream_t)stream>>>(a, sp);

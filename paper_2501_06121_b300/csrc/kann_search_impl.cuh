@@ -271,6 +271,12 @@ struct DenseBackend {
     }
   }
 
+  // a search team: every warp keeps the query in its own registers
+  __device__ __forceinline__ void init_team(const SearchArgs& a, int qi, int lane, int, int, unsigned char*,
+                                            TeamCtl*) {
+    init(a, qi, lane, nullptr);
+  }
+
   __device__ __forceinline__ void dists(const SearchArgs& a, const int* cid, int cnt, u64* ck, int lane) {
     const int lpr = lanes(a), lg = log2_lanes(a), rpi = 32 >> lg;
     const int sub = lane & (lpr - 1), grp = lane >> lg;
@@ -554,11 +560,26 @@ struct SparseBackend {
   float* qw;          // [<= SP_QMAX] weights in term order
   uint32_t trunc;
 
+  __device__ __forceinline__ void place(unsigned char* extra) {
+    bm = reinterpret_cast<uint32_t*>(extra);
+    pre = reinterpret_cast<uint16_t*>(bm + sparse_words(sp->vocab));
+    qw = reinterpret_cast<float*>(extra + sparse_query_bytes(sp->vocab) - SP_QMAX * 4);
+    trunc = 0u;
+  }
+
+  // a search team: warp 0 builds the query's tables in the team's region,
+  // every warp reads them; ends with the team at barrier 1
+  __device__ __forceinline__ void init_team(const SearchArgs& a, int qi, int lane, int w, int T, unsigned char* ws,
+                                            TeamCtl*) {
+    unsigned char* extra = WarpSmem::of(ws, a).extra;
+    if (w == 0) init(a, qi, lane, extra);
+    else place(extra);
+    team_bar(T);
+  }
+
   __device__ __forceinline__ void init(const SearchArgs& a, int qi, int lane, unsigned char* extra) {
     const int words = sparse_words(sp->vocab);
-    bm = reinterpret_cast<uint32_t*>(extra);
-    pre = reinterpret_cast<uint16_t*>(bm + words);
-    qw = reinterpret_cast<float*>(extra + sparse_query_bytes(sp->vocab) - SP_QMAX * 4);
+    place(extra);
     for (int i = lane; i < words; i += 32) bm[i] = 0u;
     __syncwarp();
     const int64_t b = sp->q_indptr[qi], e = sp->q_indptr[qi + 1];
@@ -1319,6 +1340,15 @@ __global__ void __launch_bounds__(128, MinBlocks<DT, CPLT, LEAN>::value) search_
   run_queries<decltype(be), MULTI>(a, be);
 }
 
+// A team of T warps per query (one CTA): the same rows in flight per warp
+// and the same registers per thread as the one-warp kernel.
+template <int DT, int CPLT, int MET, int LPR, int T>
+__global__ void __launch_bounds__(T * 32, MinBlocks<DT, CPLT, false>::value * 4 / T)
+    search_dense_team_kernel(const SearchArgs a) {
+  DenseBackend<DT, CPLT, false, MET, LPR> be;
+  run_queries_team<T>(a, be);
+}
+
 constexpr int PQ_TEAM = 8;  // warps sharing one query's lookup table (TeamCtl::wmax holds 8)
 
 // Teams per SM the kernel is compiled for: the uint8 table (48 KB at m = 192)
@@ -1375,6 +1405,37 @@ SearchKernelFn pick_dense_multi_t(int cplt, int metric, int lpr_exact) {
                           : pick_exact<DT, CX, false, KANN_IP, true>(lpr_exact);
   if (!f) f = metric == KANN_L2 ? pick_general<DT, KANN_L2, true>(cplt, false) : pick_general<DT, KANN_IP, true>(cplt, false);
   return f;
+}
+
+template <int DT, int MET, int T>
+SearchKernelFn pick_team(int cplt, int lpr_exact) {
+  constexpr int CX = default_chunks_per_lane(DT);
+  if (lpr_exact > 0 && cplt == CX) {
+    switch (lpr_exact) {
+      case 2: return search_dense_team_kernel<DT, CX, MET, 2, T>;
+      case 4: return search_dense_team_kernel<DT, CX, MET, 4, T>;
+      case 8: return search_dense_team_kernel<DT, CX, MET, 8, T>;
+      case 16: return search_dense_team_kernel<DT, CX, MET, 16, T>;
+      case 32: return search_dense_team_kernel<DT, CX, MET, 32, T>;
+      default: break;
+    }
+  }
+  switch (cplt) {
+    case 1: return search_dense_team_kernel<DT, 1, MET, 0, T>;
+    case 2: return search_dense_team_kernel<DT, 2, MET, 0, T>;
+    case 4: return search_dense_team_kernel<DT, 4, MET, 0, T>;
+    case 8: return search_dense_team_kernel<DT, 8, MET, 0, T>;
+    default: return nullptr;
+  }
+}
+
+// Team kernel of one storage format (team = 2 or 4 warps per query):
+// exact-tiling form at the format's default chunks per lane, else general.
+template <int DT>
+SearchKernelFn pick_dense_team_t(int cplt, int metric, int lpr_exact, int team) {
+  if (team == 2) return metric == KANN_L2 ? pick_team<DT, KANN_L2, 2>(cplt, lpr_exact) : pick_team<DT, KANN_IP, 2>(cplt, lpr_exact);
+  if (team == 4) return metric == KANN_L2 ? pick_team<DT, KANN_L2, 4>(cplt, lpr_exact) : pick_team<DT, KANN_IP, 4>(cplt, lpr_exact);
+  return nullptr;
 }
 
 template <int DT>

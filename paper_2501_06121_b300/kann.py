@@ -64,7 +64,7 @@ class kann_search_opts(ctypes.Structure):
                 ("pq_lut", ctypes.c_int32),
                 ("d_status", ctypes.c_void_p), ("d_counters", ctypes.c_void_p),
                 ("d_work_counter", ctypes.c_void_p), ("d_n", ctypes.c_void_p),
-                ("visited_format", ctypes.c_int32), ("expand", ctypes.c_int32)]
+                ("visited_format", ctypes.c_int32), ("expand", ctypes.c_int32), ("team", ctypes.c_int32)]
 
 
 _L = None
@@ -217,7 +217,7 @@ KANN_PQ_LUT_F32, KANN_PQ_LUT_F16, KANN_PQ_LUT_U8 = 0, 1, 2
 
 
 def _opts(rerank=0, max_hops=0, hash_bits=0, warps_per_block=0, lanes_per_row=0, status=None, counters=None,
-          work_counter=None, n_device=None, lean=0, pq_lut_f16=0, visited_format=0, expand=0, pq_lut=None):
+          work_counter=None, n_device=None, lean=0, pq_lut_f16=0, visited_format=0, expand=0, pq_lut=None, team=0):
     _require_cuda(status, counters, work_counter, n_device)
     p = lambda t: t.data_ptr() if t is not None else None
     if pq_lut is None:  # pq_lut_f16=1 is the FP16 table
@@ -225,7 +225,7 @@ def _opts(rerank=0, max_hops=0, hash_bits=0, warps_per_block=0, lanes_per_row=0,
     return kann_search_opts(int(rerank), int(max_hops), int(hash_bits), int(warps_per_block), int(lanes_per_row),
                             int(lean), int(pq_lut),
                             p(status), p(counters), p(work_counter), p(n_device), int(visited_format),
-                            int(expand))
+                            int(expand), int(team))
 
 
 def kann_search(index, queries, k, ef, ids=None, dists=None, stream=None):

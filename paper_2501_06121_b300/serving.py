@@ -165,14 +165,15 @@ class SearchServer:
         need = self.page_bytes[name]
         if self.live_bytes() + need <= self.budget and len(self.pages) < self.max_pages:
             return self._new_page(name)
-        # release idle pages of other indices that have nothing waiting, least
-        # recently used first (a page of an index with waiting requests is
-        # about to be used again: taking it would only trade captures)
-        idle = sorted((p for p in self.pages if p.busy is None and p.name != name and not pending[p.name]),
-                      key=lambda p: p.last_used)
-        for p in idle:
-            if self.live_bytes() + need <= self.budget and len(self.pages) < self.max_pages:
-                break
+        # release idle pages of other indices that have nothing waiting (a
+        # page of an index with waiting requests is about to be used again:
+        # taking it would only trade captures); an index's last page goes
+        # only after every spare one, least recently used first
+        idle = [p for p in self.pages if p.busy is None and p.name != name and not pending[p.name]]
+        while idle and not (self.live_bytes() + need <= self.budget and len(self.pages) < self.max_pages):
+            held = collections.Counter(q.name for q in self.pages)
+            p = min(idle, key=lambda q: (held[q.name] <= 1, q.last_used))
+            idle.remove(p)
             self.pages.remove(p)
             self.stats["pages_released"] += 1
         if self.live_bytes() + need <= self.budget and len(self.pages) < self.max_pages:

@@ -62,3 +62,28 @@ def test_upload_rejects_inconsistent_graph_on_host():
     assert L.kann_index_upload(ctypes.byref(h), ctypes.byref(g), ctypes.byref(v), ctypes.byref(two_sources), None, None, 0) == K.KANN_EINVAL
     e4m3_no_scale = K.kann_vectors_desc(K.KANN_E4M3, 128, K.KANN_L2, 0, 16, None, 128)
     assert L.kann_index_upload(ctypes.byref(h), ctypes.byref(g), ctypes.byref(e4m3_no_scale), None, None, None, 0) == K.KANN_EINVAL
+
+
+def test_binding_struct_layouts_match_the_header(tmp_path):
+    # every struct the binding passes by pointer has the header's size and
+    # field offsets (a field appended on one side only would shift nothing
+    # visible until a search read garbage options)
+    import subprocess
+    from paper_2501_06121_b300 import kann as K
+    structs = [K.kann_graph_desc, K.kann_vectors_desc, K.kann_pq_desc, K.kann_sparse_desc, K.kann_search_opts]
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "kann.h"', "int main(void) {"]
+    for S in structs:
+        lines.append('  printf("%%s %%zu\\n", "%s", sizeof(%s));' % (S.__name__, S.__name__))
+        for name, _ in S._fields_:
+            lines.append('  printf("%%s.%%s %%zu\\n", "%s", "%s", offsetof(%s, %s));' % (S.__name__, name, S.__name__, name))
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(l.rsplit(" ", 1) for l in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                        text=True).stdout.split("\n") if l)
+    for S in structs:
+        assert int(got[S.__name__]) == ctypes.sizeof(S), S.__name__
+        for name, _ in S._fields_:
+            assert int(got["%s.%s" % (S.__name__, name)]) == getattr(S, name).offset, (S.__name__, name)

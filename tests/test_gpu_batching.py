@@ -134,7 +134,8 @@ def test_autotuner_returns_result_preserving_settings(two_indices, tmp_path):
     Qd = dev(Q[:500])
     cache = str(tmp_path / "tune.json")
     opts = A.tune(idx, Qd, 10, 64, reps=2, cache_path=cache)
-    assert set(opts) == {"lanes_per_row", "hash_bits", "visited_format", "warps_per_block", "lean", "persistent"}
+    assert set(opts) == {"lanes_per_row", "hash_bits", "visited_format", "warps_per_block", "lean", "team",
+                         "persistent"}
     a_i, a_d = A.search_with(idx, Qd, 10, 64, opts)
     b_i, b_d = K.kann_search_ex(idx, Qd, 10, 64)
     torch.cuda.synchronize()

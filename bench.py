@@ -372,7 +372,8 @@ def run_serving(dev, args):
 
     acc = {"10kx128": accuracy("10kx128", small, X1d, Q1, K_.KANN_L2, X1),
            "768": accuracy("768", big, X7d, Q7, K_.KANN_IP, X7d.cpu().numpy())}
-    spec = dict(kmax=100, efmax=512, opts=dict(rerank=-1))
+    # dense indices: `--serving-team` warps per query (0 = one warp)
+    spec = dict(kmax=100, efmax=512, opts=dict(rerank=-1, team=args.serving_team))
     runs = [("e4m3_rerank", {"10kx128": dict(spec, index=small, d=128), "768": dict(spec, index=big, d=768)})]
     if args.serving_pq:
         cb = K_.kann_pq_train(X7d[:min(n7, 100_000)].contiguous(), 192, iters=25, seed=3)
@@ -388,12 +389,15 @@ def run_serving(dev, args):
                               "(%.0f s incl. data)" % (n7, build7)},
            "traversal": "FP8 E4M3 per-vector scale + FP32 re-rank (R = ef)", "k": [10, 100], "ef": [64, 512],
            "seconds_per_rate": args.serving_seconds, "memory_budget": args.serving_memory,
+           "team": args.serving_team,
            "accuracy_vs_fp64_oracle": acc, "runs": []}
     Q7h = Q7
     for run_name, indices in runs:
-        srv = S.SearchServer(indices, page_capacity=2048, memory_budget=args.serving_memory, max_pages=8)
+        tq = None if args.serving_no_tune else {"10kx128": torch_from(Q1[:500], dev), "768": torch_from(Q7h[:500], dev)}
+        srv = S.SearchServer(indices, page_capacity=2048, memory_budget=args.serving_memory, max_pages=8,
+                             tune_queries=tq)
         srv.prepare({"10kx128": 2, "768": 2})
-        res = {"run": run_name, "page_capacity": srv.caps, "rates": []}
+        res = {"run": run_name, "page_capacity": srv.caps, "launch_settings_tuned": srv.tuned, "rates": []}
         for i, rate in enumerate(float(r) for r in args.serving_rates.split(",")):
             reqs = S.poisson_requests(rate, args.serving_seconds, {"10kx128": Q1, "768": Q7h}, seed=100 + i)
             done = srv.run(reqs, time_limit=args.serving_seconds * 3 + 10)
@@ -658,25 +662,55 @@ def run_big(args):
         return e0.elapsed_time(e1) / reps, out
 
     rows = []
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except Exception:
+        pass
+    hbm = peaks.get("hbm_gbs", 6400.0)
+
+    def work(index, ef, **o):
+        # mean per-query counters with a visited table that never forgets:
+        # layer-0 evaluations, expansions, upper evaluations, upper hops
+        cnt = torch.zeros((len(Q), 4), dtype=torch.int32, device=dev)
+        K_.kann_search_ex(index, Qd, 10, ef, counters=cnt, hash_bits=15, visited_format=K_.KANN_VISITED_COMPACT, **o)
+        torch.cuda.synchronize()
+        return cnt.double().mean(0).cpu().numpy()
+
     torch.cuda.nvtx.range_push("search")  # the sweep, apart from the build (for a profiler)
-    for ef in (16, 32, 48, 64, 128, 256):
+    for ef in (16, 32, 48, 64, 128, 256, 512, 1024):
+        # algorithmic bytes per query (row bytes x evaluations, adjacency rows,
+        # the query, the output; PQ: 192-byte codes plus the re-rank rows)
+        c32 = work(idx32, ef)
+        b32 = (c32[0] + c32[2]) * d * 4 + c32[1] * 64 * 4 + c32[3] * 32 * 4 + d * 4 + 10 * 8
+        c8 = work(idx_pq, ef, rerank=100, pq_lut=K_.KANN_PQ_LUT_U8)
+        b8 = (c8[0] + c8[2]) * 192 + c8[1] * 64 * 4 + c8[3] * 32 * 4 + d * 4 + 10 * 8 + min(100, ef) * d * 4
         ms8, (i8, _) = timed(lambda: K_.kann_search_ex(idx_pq, Qd, 10, ef, rerank=100, pq_lut=K_.KANN_PQ_LUT_U8))
         msb, (ib, _) = timed(lambda: K_.kann_search_ex(idx_pqb, Qd, 10, ef, rerank=100, pq_lut=K_.KANN_PQ_LUT_U8))
+        # re-rank of every beam entry (R = ef): lifts the cap a fixed R puts on recall
+        mse, (ie, _) = timed(lambda: K_.kann_search_ex(idx_pq, Qd, 10, ef, rerank=-1, pq_lut=K_.KANN_PQ_LUT_U8))
         o32, ms32, (i32, _) = fastest(lambda **o: K_.kann_search_ex(idx32, Qd, 10, ef, **o),
-                                      [dict(team=t, hash_bits=hb) for t in (0, 2, 4) for hb in (0, 13)])
+                                      [dict(team=t, hash_bits=hb) for t in (0, 2, 4) for hb in (0, 13, 14)])
         rows.append({"ef": ef, "pq_u8table_rerank100_qps": 1e4 / (ms8 / 1e3),
                      "pq_u8table_rerank100_recall": recall_at(i8.cpu().numpy()[:ngt], gt),
                      "pq_u8table_bf16rerank100_qps": 1e4 / (msb / 1e3),
                      "pq_u8table_bf16rerank100_recall": recall_at(ib.cpu().numpy()[:ngt], gt),
+                     "pq_u8table_rerank_ef_qps": 1e4 / (mse / 1e3),
+                     "pq_u8table_rerank_ef_recall": recall_at(ie.cpu().numpy()[:ngt], gt),
                      "fp32_qps": 1e4 / (ms32 / 1e3), "fp32_recall": recall_at(i32.cpu().numpy()[:ngt], gt),
-                     "fp32_launch": o32})
+                     "fp32_launch": o32, "fp32_rows_evaluated_per_query": c32[0] + c32[2],
+                     "fp32_algorithmic_bytes_per_query": b32,
+                     "fp32_roofline_frac": 1e4 * b32 / (ms32 / 1e3) / 1e9 / hbm,
+                     "pq_rows_evaluated_per_query": c8[0] + c8[2], "pq_u8_algorithmic_bytes_per_query": b8,
+                     "pq_u8_roofline_frac": 1e4 * b8 / (ms8 / 1e3) / 1e9 / hbm})
         print(json.dumps(rows[-1]), flush=True)
     torch.cuda.nvtx.range_pop()
     dev_bytes = {"fp32_rows": n * d * 4, "bf16_rerank_rows": n * d * 2, "pq_codes": n * 192,
                  "graph_layer0": n * 64 * 4}
     print(json.dumps({"workload": "msmarco_dense", "n": n, "d": d, "data_gen_s": gen_s, "graph_build_s": build_s,
                       "graph_builder": "device", "pq_train_encode_s": pq_s, "ground_truth_s_1000q": gt_s,
-                      "device_bytes": dev_bytes, "rows": rows}))
+                      "device_bytes": dev_bytes, "peak_gbs": hbm, "rows": rows}))
 
 
 SEARCH_KERNEL_SOURCES = ("kann_device.cuh", "kann_internal.h", "kann_search_impl.cuh", "kann_search_f16.cu")
@@ -722,6 +756,8 @@ def main():
     ap.add_argument("--serving-768-n", type=int, default=1_000_000)
     ap.add_argument("--serving-pq", action="store_true", help="also serve the 768-d index with PQ codes")
     ap.add_argument("--serving-memory", type=int, default=48 << 20)
+    ap.add_argument("--serving-team", type=int, default=0, help="warps per query of the dense served indices")
+    ap.add_argument("--serving-no-tune", action="store_true", help="serve with default launch settings")
     ap.add_argument("--serving-rates", default="5000,20000,50000,100000,200000")
     ap.add_argument("--workload", default="sift1m",
                     choices=["sift1m", "pq768", "sparse", "sparse100k", "serving", "msmarco_dense"])
@@ -838,17 +874,21 @@ def main():
     tune_s = time.time() - t_tune
     kw16, kw32 = launch_kwargs(tuned16, work_ctr), launch_kwargs(tuned32, work_ctr)
 
-    def timed(index, rr, steps, warm, kw):
+    def timed(index, rr, steps, warm, kw, label):
         for _ in range(warm):
             K_.kann_search_ex(index, Qd, K, ef, ids=ids_buf, dists=d_buf, rerank=rr, **kw)
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
         evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+        # the timed launches in an NVTX range of their own (a profiler can
+        # select exactly these)
+        torch.cuda.nvtx.range_push(label)
         evs[0].record(stream)
         for i in range(steps):
             K_.kann_search_ex(index, Qd, K, ef, ids=ids_buf, dists=d_buf, rerank=rr, **kw)
             evs[i + 1].record(stream)
+        torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
         per = [evs[i].elapsed_time(evs[i + 1]) for i in range(steps)]
         return sum(per), per
@@ -856,10 +896,10 @@ def main():
     clocks = Clocks(local)
     time.sleep(0.3)
     w0 = time.time()
-    total_ms, per = timed(idx16, -1, args.steps, args.warmup, kw16)
+    total_ms, per = timed(idx16, -1, args.steps, args.warmup, kw16, "timed_fp16")
     clk = clocks.stop(w0 + 1e-3 * 0, time.time())
     total_ms = max_over_ranks(total_ms, world, dev)
-    fp32_ms, _ = timed(idx32, 0, max(3, args.steps // 2), 2, kw32)
+    fp32_ms, _ = timed(idx32, 0, max(3, args.steps // 2), 2, kw32, "timed_fp32")
     fp32_ms /= max(3, args.steps // 2)
 
     qps = job_qps(world, N_QUERY, args.steps, total_ms)

@@ -41,18 +41,20 @@ def _time(index, Q, k, ef, reps, opts):
     return e0.elapsed_time(e1) / reps, out
 
 
-def tune(index, queries, k, ef, rerank=0, reps=5, cache_path=None, verbose=False):
+def tune(index, queries, k, ef, rerank=0, reps=5, cache_path=None, verbose=False, fixed=None):
     """Returns the fastest result-preserving option dict for kann_search_ex
     (keys lanes_per_row, hash_bits, visited_format, warps_per_block, lean,
-    team, persistent)."""
-    key = _signature(index, k, ef, rerank)
+    team, persistent).  `fixed`: options every trial runs with (such as a PQ
+    table format), not tuned and not returned."""
+    fixed = {key: v for key, v in (fixed or {}).items() if key not in ("rerank", "persistent")}
+    key = _signature(index, k, ef, rerank) + "|" + json.dumps(fixed, sort_keys=True)
     cache = {}
     if cache_path and os.path.exists(cache_path):
         with open(cache_path) as f:
             cache = json.load(f)
         if key in cache:
             return dict(cache[key]["opts"])
-    base_t, (ref_i, ref_d) = _time(index, queries, k, ef, reps, dict(rerank=rerank))
+    base_t, (ref_i, ref_d) = _time(index, queries, k, ef, reps, dict(fixed, rerank=rerank))
     best = dict(lanes_per_row=0, hash_bits=0, visited_format=0, warps_per_block=0, lean=0, team=0,
                 persistent=False)
     best_t = base_t
@@ -61,7 +63,7 @@ def tune(index, queries, k, ef, rerank=0, reps=5, cache_path=None, verbose=False
     def trial(o):
         nonlocal best, best_t
         try:
-            t, (ids, d) = _time(index, queries, k, ef, reps, dict(o, rerank=rerank))
+            t, (ids, d) = _time(index, queries, k, ef, reps, dict(fixed, **o, rerank=rerank))
         except K.KannError:
             return
         same = torch.equal(ids, ref_i) and torch.equal(d, ref_d)

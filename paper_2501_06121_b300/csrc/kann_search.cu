@@ -1,7 +1,9 @@
 // kann_search.cu -- launchers of the batched HNSW search kernels, and the PQ
 // and sparse kernels (the dense kernels are compiled per storage format in
-// kann_search_{f32,f16,bf16,e4m3}.cu; all device code is kann_search_impl.cuh).
+// kann_search_{f32,f16,bf16,e4m3}.cu; the device code is kann_search_impl.cuh
+// and, for the sparse back-end, kann_search_sparse.cuh).
 #include "kann_search_impl.cuh"
+#include "kann_search_sparse.cuh"
 
 namespace kann {
 namespace {

@@ -1,6 +1,7 @@
 // kann_search_impl.cuh -- batched HNSW search kernels for sm_103a (device code,
 // included by the per-format translation units kann_search_{f32,f16,bf16,e4m3}.cu
-// and by kann_search.cu, which holds the PQ and sparse kernels and the launchers).
+// and by kann_search.cu, which holds the PQ and sparse kernels and the launchers;
+// the sparse back-end is kann_search_sparse.cuh).
 //
 // One warp searches one query (HNSW K-NN-SEARCH, Malkov & Yashunin Alg. 5,
 // the index of kANNolo Sec. 2):
@@ -532,125 +533,6 @@ struct PQBackend {
   }
 };
 
-// ---------------------------------------------------------------------------
-// Sparse back-end (inner product over term/weight lists).  The query is held
-// as a presence bitmap over the vocabulary, per-word prefix counts of set
-// bits, and its weights in term order: query terms are sorted and unique, so
-// the rank of a present term t -- the number of query terms below it, i.e.
-// prefix[t / 32] + popcount of word t / 32 below bit t % 32 -- is its index
-// in the weight array.  Each candidate document's term list is walked by a
-// group of 8 lanes, each lane summing w_q(t) * w_x(t) over its positions in
-// order; distance = -sum.  A query keeps its first 512 terms (flagged
-// otherwise); terms >= vocab never match.
-// ---------------------------------------------------------------------------
-constexpr int SP_QMAX = 512;  // query terms kept
-constexpr int SP_LPD = 8;     // lanes per document
-
-__host__ __device__ constexpr int sparse_words(int vocab) { return (vocab + 31) / 32; }
-// bytes of a query's tables: bitmap (4 per word), prefix counts (2 per word,
-// rounded to 4), weights
-__host__ __device__ constexpr int sparse_query_bytes(int vocab) {
-  return sparse_words(vocab) * 4 + (sparse_words(vocab) * 2 + 3) / 4 * 4 + SP_QMAX * 4;
-}
-
-struct SparseBackend {
-  const SparseArgs* sp;
-  uint32_t* bm;       // [words] presence bits
-  uint16_t* pre;      // [words] set bits in the words before
-  float* qw;          // [<= SP_QMAX] weights in term order
-  uint32_t trunc;
-
-  __device__ __forceinline__ void place(unsigned char* extra) {
-    bm = reinterpret_cast<uint32_t*>(extra);
-    pre = reinterpret_cast<uint16_t*>(bm + sparse_words(sp->vocab));
-    qw = reinterpret_cast<float*>(extra + sparse_query_bytes(sp->vocab) - SP_QMAX * 4);
-    trunc = 0u;
-  }
-
-  // a search team: warp 0 builds the query's tables in the team's region,
-  // every warp reads them; ends with the team at barrier 1
-  __device__ __forceinline__ void init_team(const SearchArgs& a, int qi, int lane, int w, int T, unsigned char* ws,
-                                            TeamCtl*) {
-    unsigned char* extra = WarpSmem::of(ws, a).extra;
-    if (w == 0) init(a, qi, lane, extra);
-    else place(extra);
-    team_bar(T);
-  }
-
-  __device__ __forceinline__ void init(const SearchArgs& a, int qi, int lane, unsigned char* extra) {
-    const int words = sparse_words(sp->vocab);
-    place(extra);
-    for (int i = lane; i < words; i += 32) bm[i] = 0u;
-    __syncwarp();
-    const int64_t b = sp->q_indptr[qi], e = sp->q_indptr[qi + 1];
-    const int nt = e - b < SP_QMAX ? (int)(e - b) : SP_QMAX;
-    trunc = e - b > SP_QMAX ? 1u : 0u;
-    for (int j = lane; j < nt; j += 32) {
-      const uint32_t t = sp->q_terms[b + j];
-      if (t < (uint32_t)sp->vocab) atomicOr(bm + (t >> 5), 1u << (t & 31));
-    }
-    __syncwarp();
-    // prefix counts: each lane a contiguous block of words, then a warp scan
-    const int per = (words + 31) / 32, w0 = lane * per, w1 = min(words, w0 + per);
-    int c = 0;
-    for (int i = w0; i < w1; ++i) c += __popc(bm[i]);
-    int incl = c;
-    for (int o = 1; o < 32; o <<= 1) {
-      const int v = __shfl_up_sync(FULL, incl, o);
-      if (lane >= o) incl += v;
-    }
-    int run = incl - c;
-    for (int i = w0; i < w1; ++i) {
-      pre[i] = (uint16_t)run;
-      run += __popc(bm[i]);
-    }
-    // weights in term order (terms >= vocab, which never match, keep their
-    // slots so that the ranks of the others stay their positions)
-    for (int j = lane; j < nt; j += 32) qw[j] = sp->q_w[b + j];
-    __syncwarp();
-  }
-
-  __device__ __forceinline__ void dists(const SearchArgs&, const int* cid, int cnt, u64* ck, int lane) {
-    const int sub = lane & (SP_LPD - 1), grp = lane / SP_LPD;
-    constexpr int DPI = 32 / SP_LPD;  // documents per warp iteration
-    const uint32_t vocab = (uint32_t)sp->vocab;
-    for (int base = 0; base < cnt; base += DPI) {
-      const int r = base + grp;
-      const int id = r < cnt ? cid[r] : -1;
-      float acc = 0.f;
-      if (id >= 0) {
-        const int64_t b = __ldg(sp->indptr + id);
-        const int len = (int)(__ldg(sp->indptr + id + 1) - b);
-        const uint16_t* tp = sp->terms + b;
-        const float* wp = sp->w + b;
-        for (int t0 = sub; t0 < len; t0 += 4 * SP_LPD) {
-          uint32_t tm[4];
-          float wx[4];
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int t = t0 + u * SP_LPD;
-            tm[u] = t < len ? (uint32_t)__ldg(tp + t) : 0xffffffffu;
-            wx[u] = t < len ? __ldg(wp + t) : 0.f;
-          }
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const uint32_t t = tm[u];
-            if (t < vocab) {
-              const uint32_t wd = bm[t >> 5];
-              if ((wd >> (t & 31)) & 1u) {
-                const int rk = pre[t >> 5] + __popc(wd & ((1u << (t & 31)) - 1u));
-                acc = fmaf(qw[rk], wx[u], acc);
-              }
-            }
-          }
-        }
-      }
-      for (int o = SP_LPD >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(FULL, acc, o);
-      if (sub == 0 && r < cnt) ck[r] = make_key(-acc, (uint32_t)id);
-    }
-  }
-};
-
 // Exact FP32 distances for the re-rank, from the index's FP32 copy.  Same
 // lane/chunk mapping and summation order as the FP32 dense back-end (chunks
 // in order, even and odd elements in two partial sums, their sum, then the
@@ -903,6 +785,8 @@ __device__ __forceinline__ void merge_batch(u64 e0, u64 e1, u64* W, int& len, in
   if (lo < cursor) cursor = lo;
 }
 
+// Per-query status bits a back-end reports (the sparse back-end's truncated
+// query; found by argument-dependent lookup where a back-end defines one).
 template <class B>
 __device__ __forceinline__ uint32_t backend_status(const B&) { return 0u; }
 
@@ -912,9 +796,6 @@ template <class B>
 __device__ __forceinline__ float backend_out_dist(const B&, float d) { return d; }
 template <int CPL, int LF>
 __device__ __forceinline__ float backend_out_dist(const PQBackend<CPL, LF>& b, float d) { return b.out_dist(d); }
-__device__ __forceinline__ uint32_t backend_status(const SparseBackend& b) {
-  return b.trunc ? KANN_QSTAT_QUERY_TRUNCATED : 0u;
-}
 
 // One step of the multi-expansion layer-0 search (a batched variant of the
 // HNSW step, under its own oracle form; not the parity search): the

@@ -118,14 +118,25 @@ class SearchServer:
     page_capacity: queries per batch (halved for an index until one page fits
     the budget); memory_budget: device bytes all live pages may count
     together (each page counts kann_search_workspace_bytes of its capacity);
-    max_pages: streams in flight at most."""
+    max_pages: streams in flight at most.  tune_queries ({name: device
+    [m, d] FP32 queries}, dense and PQ indices): the index's launch settings
+    are chosen by the autotuner on those queries at k = min(10, kmax) and
+    ef = efmax / 2 (result-preserving settings only; `tuned` records them)."""
 
     def __init__(self, indices, page_capacity=1024, memory_budget=1 << 30, max_pages=16, device="cuda",
-                 search_opts=None):
-        self.specs, self.caps, self.page_bytes = {}, {}, {}
+                 search_opts=None, tune_queries=None):
+        self.specs, self.caps, self.page_bytes, self.tuned = {}, {}, {}, {}
         self.device, self.budget, self.max_pages = device, memory_budget, max_pages
         for name, spec in indices.items():
             opts = dict(search_opts or {}, **spec.get("opts", {}))
+            if tune_queries and name in tune_queries:
+                from . import autotune
+                k = min(10, spec["kmax"])
+                got = autotune.tune(spec["index"], tune_queries[name], k, max(k, spec["efmax"] // 2),
+                                    rerank=opts.get("rerank", 0), reps=3, fixed=opts)
+                got.pop("persistent", None)
+                self.tuned[name] = got
+                opts.update({key: v for key, v in got.items() if v})
             opts.pop("persistent", None)  # pages always launch the persistent form
             size = lambda c: K.kann_search_workspace_bytes(spec["index"], c, spec["kmax"], spec["efmax"], **opts)
             cap = page_capacity

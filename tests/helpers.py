@@ -99,3 +99,55 @@ def recall(ids, gt_ids, k):
 
 def id_set_match_fraction(a, b):
     return float(np.mean([set(x) == set(y) for x, y in zip(a, b)]))
+
+
+def random_graph(n, M, levels, seed):
+    """A seeded random HNSW-shaped graph over n nodes (an input, like the
+    data: search parity holds on any graph, navigable or not): the given
+    levels, layer-0 lists of 2M distinct random other nodes, and for every
+    layer l >= 1 lists of min(M, nodes on l - 1) distinct random other nodes
+    of that layer; the entry point is the lowest id on the top layer."""
+    rng = np.random.default_rng(seed)
+    M0 = 2 * M
+    levels = np.asarray(levels, np.int8)
+    L = int(levels.max()) if n else 0
+
+    def rows(cands):
+        # for each node of cands, min(M, |cands| - 1) distinct other nodes of cands
+        m = min(M, len(cands) - 1)
+        out = np.empty((len(cands), m), np.int64)
+        for i in range(len(cands)):
+            pick = rng.choice(len(cands) - 1, m, replace=False)
+            out[i] = pick + (pick >= i)  # skip position i (the node itself)
+        return cands[out]
+
+    l0 = np.full((n, M0), -1, np.int32)
+    m0 = min(M0, n - 1)
+    if m0 * m0 > n // 8:
+        # small n: distinct draws per row
+        picks = np.stack([rng.choice(n - 1, m0, replace=False) for _ in range(n)]) if n > 1 else \
+            np.zeros((n, 0), np.int64)
+    else:
+        # large n: independent draws, the few rows with a repeat drawn again
+        # (a row repeats with probability below 1/16 here)
+        picks = rng.integers(0, n - 1, (n, m0))
+        while True:
+            srt = np.sort(picks, axis=1)
+            bad = np.nonzero((srt[:, 1:] == srt[:, :-1]).any(axis=1))[0]
+            if len(bad) == 0:
+                break
+            picks[bad] = rng.integers(0, n - 1, (len(bad), m0))
+    picks = picks + (picks >= np.arange(n)[:, None])
+    l0[:, :m0] = picks
+    upper_nodes = np.nonzero(levels >= 1)[0]
+    slot = np.full(n, -1, np.int32)
+    slot[upper_nodes] = np.arange(len(upper_nodes), dtype=np.int32)
+    upper = np.full((max(len(upper_nodes), 1), max(L, 1), M), -1, np.int32)
+    for layer in range(1, L + 1):
+        on = np.nonzero(levels >= layer)[0]
+        if len(on) < 2:
+            continue
+        r = rows(on)
+        upper[slot[on], layer - 1, :r.shape[1]] = r
+    entry = int(np.nonzero(levels == L)[0][0])
+    return dict(n=n, M=M, M0=M0, max_level=L, entry=entry, level=levels, l0=l0, upper_slot=slot, upper=upper)

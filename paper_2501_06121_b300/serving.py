@@ -247,6 +247,56 @@ class SearchServer:
         return done
 
 
+class HostBatchPipeline:
+    """Searches batches whose queries and results live in pinned host memory,
+    with the copies overlapped: batch i's host-to-device copy runs on one copy
+    stream while batch i - 1 searches, and batch i - 1's results come back on
+    a second copy stream while batch i searches (two sets of device buffers
+    alternate; events order every reuse).  Each batch is one kann_search_ex
+    call with the given options; results equal those of that call."""
+
+    def __init__(self, index, n, d, k, ef, device="cuda", **opts):
+        self.index, self.n, self.k, self.ef, self.opts = index, n, k, ef, dict(opts)
+        self.streams = [torch.cuda.Stream(device) for _ in range(3)]  # h2d, search, d2h
+        self.q = [torch.empty((n, d), dtype=torch.float32, device=device) for _ in range(2)]
+        self.ids = [torch.empty((n, k), dtype=torch.int32, device=device) for _ in range(2)]
+        self.dists = [torch.empty((n, k), dtype=torch.float32, device=device) for _ in range(2)]
+        ev = lambda: [torch.cuda.Event(), torch.cuda.Event()]
+        self.ev_h2d, self.ev_search, self.ev_d2h = ev(), ev(), ev()
+        self.i = 0
+
+    def submit(self, q_host, ids_host, dists_host):
+        """Queue batch q_host [n, d] (pinned FP32); its ids and distances land
+        in ids_host / dists_host (pinned) once the d2h stream passes them."""
+        hs, ss, ds = self.streams
+        b = self.i & 1
+        hs.wait_event(self.ev_search[b])  # the search two batches back has read q[b]
+        with torch.cuda.stream(hs):
+            self.q[b].copy_(q_host, non_blocking=True)
+        self.ev_h2d[b].record(hs)
+        ss.wait_event(self.ev_h2d[b])
+        ss.wait_event(self.ev_d2h[b])  # the results two batches back have left ids[b]
+        K.kann_search_ex(self.index, self.q[b], self.k, self.ef, ids=self.ids[b], dists=self.dists[b], stream=ss,
+                         **self.opts)
+        self.ev_search[b].record(ss)
+        ds.wait_event(self.ev_search[b])
+        with torch.cuda.stream(ds):
+            ids_host.copy_(self.ids[b], non_blocking=True)
+            dists_host.copy_(self.dists[b], non_blocking=True)
+        self.ev_d2h[b].record(ds)
+        self.i += 1
+
+    def first_stream(self):
+        return self.streams[0]
+
+    def last_stream(self):
+        return self.streams[2]
+
+    def synchronize(self):
+        for st in self.streams:
+            st.synchronize()
+
+
 def status_counts(done):
     """How many finished requests carry each KANN_QSTAT_* bit."""
     names = {"hop_cap": K.KANN_QSTAT_HOPCAP, "forgot": K.KANN_QSTAT_FORGOT, "bad_id": K.KANN_QSTAT_BAD_ID,

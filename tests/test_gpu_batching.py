@@ -168,3 +168,23 @@ def test_admission_bytes_follow_the_settings(two_indices):
     assert len(done) == len(reqs) and srv.stats["peak_bytes"] <= per_page and len(srv.pages) == 1
     with pytest.raises(ValueError):
         S.SearchServer({"a": dict(index=idx_a, d=128, kmax=10, efmax=K.KANN_MAX_EF + 1)})
+
+
+def test_host_batch_pipeline_equals_single_calls(two_indices):
+    # batches from pinned host memory with copies overlapped on two copy
+    # streams: each batch's results equal one kann_search_ex call's
+    idx, Q, _ = two_indices["a"]
+    n = 200
+    pipe = S.HostBatchPipeline(idx, n, 128, 10, 64)
+    outs = []
+    for b in range(5):
+        qh = torch.from_numpy(np.ascontiguousarray(Q[b * n:(b + 1) * n])).pin_memory()
+        ih = torch.empty((n, 10), dtype=torch.int32).pin_memory()
+        dh = torch.empty((n, 10), dtype=torch.float32).pin_memory()
+        pipe.submit(qh, ih, dh)
+        outs.append((qh, ih, dh))
+    pipe.synchronize()
+    for qh, ih, dh in outs:
+        ri, rd = K.kann_search_ex(idx, qh.cuda(), 10, 64)
+        torch.cuda.synchronize()
+        assert torch.equal(ih, ri.cpu()) and torch.equal(dh, rd.cpu())

@@ -94,7 +94,7 @@ def test_pq_m192_parity(set768, ef, lut_f16):
 
 @pytest.mark.parametrize("ef", [128, 1000])
 def test_pq_m192_u8_table_bit_exact(set768, ef):
-    # the uint8 table at m = 192 (48 KB, three teams per SM): identical
+    # the uint8 table at m = 192 (48 KB, four teams per SM): identical
     # integer decisions on both sides
     X, Q, g, cb, codes = set768
     idx = pq_index(g, cb, codes, K.KANN_IP)

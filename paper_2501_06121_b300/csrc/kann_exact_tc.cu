@@ -6,25 +6,28 @@
 // and keeps each query's k best (distance, id) pairs in registers; the scores
 // are never written to HBM.
 //
-// One persistent CTA per SM walks work items (a tile of 128 queries x one
-// split of the base).  Roles inside a CTA (320 threads):
-//   warp 0      TMA producer: per base tile of 256 rows and per 64-element K
-//               chunk, loads the base chunk (256 x 64), 128-byte swizzled,
-//               into a stage ring; for d <= 256 the item's 128 x d query block
-//               is loaded once per item and stays resident (the MMAs of every
-//               tile read it), otherwise each stage carries its query chunk
-//               (128 x 64) too;
-//   warp 1      allocates 512 TMEM columns (two 128 x 256 FP32 accumulators)
-//               and issues tcgen05.mma (M=128, N=256, K=16) from one lane;
-//               tcgen05.commit frees a ring stage when its MMAs are done and
-//               signals a full accumulator;
-//   warps 2..9  two epilogue warpgroups: thread r of group g owns query row r
-//               (TMEM lane r) over columns [128 g, 128 g + 128) of each tile,
+// One persistent CTA per SM walks work items (two tiles of 128 queries x one
+// split of the base: both query blocks use each staged base tile, which halves
+// the base traffic from L2 per score).  Roles inside a CTA (320 threads):
+//   warp 0      TMA producer: per base tile of 128 rows and per 64-element K
+//               chunk, loads the base chunk (128 x 64), 128-byte swizzled,
+//               into a stage ring; for d <= 256 (when shared memory allows)
+//               the item's two 128 x d query blocks are loaded once per item
+//               and stay resident (the MMAs of every tile read them),
+//               otherwise each stage carries their two query chunks
+//               (2 x 128 x 64) too;
+//   warp 1      allocates 512 TMEM columns (two buffers, each holding one
+//               128 x 128 FP32 accumulator per query block) and issues
+//               tcgen05.mma (M=128, N=128, K=16) from one lane, one per query
+//               block and K step on the same base chunk; tcgen05.commit frees
+//               a ring stage when its MMAs are done and signals a full buffer;
+//   warps 2..9  two epilogue warpgroups: thread r of group g owns row r of
+//               query block g (TMEM lane r) over the 128 columns of each tile,
 //               reads its scores with tcgen05.ld into registers, filters them
 //               against its current k-th distance and inserts the survivors
 //               into its own top-k list in shared memory.
-// The scans of one query (its 2 S column-half x split lists, on different
-// CTAs) share an upper bound on its k-th score in global memory: it starts
+// The scans of one query (its S split lists, on different CTAs) share an
+// upper bound on its k-th score in global memory: it starts
 // from tc_threshold_kernel's bound (a strided sample of the base scored on the
 // CUDA cores), every list that is full lowers it (atomicMin) to just above its
 // own k-th score, and each scan filters against the smaller of that bound and
@@ -46,13 +49,14 @@ namespace kann {
 namespace {
 
 constexpr int TC_M = 128;       // queries per work item (TMEM lanes)
-constexpr int TC_N = 256;       // base rows per tile (accumulator columns)
+constexpr int TC_N = 128;       // base rows per tile (accumulator columns)
+constexpr int TC_QB = 2;        // query blocks of TC_M rows per work item (share each base tile)
 constexpr int TC_K = 64;        // K elements per stage: one 128-byte swizzle row
 constexpr int TC_MAX_STAGES = 6;
 constexpr int TC_QRES_MAX_KCHUNKS = 4;  // resident query block up to d = 256
 constexpr int A_BYTES = TC_M * TC_K * 2;
 constexpr int B_BYTES = TC_N * TC_K * 2;
-constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int STAGE_BYTES = TC_QB * A_BYTES + B_BYTES;
 constexpr int TC_EPI_WARPS = 8;     // two warpgroups, one per half of a tile's columns
 constexpr int TC_THREADS = 64 + 32 * TC_EPI_WARPS;
 constexpr uint32_t TMEM_COLS = 512;
@@ -331,7 +335,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       uint32_t it = 0, iq = 0;
       bool ok = true;
       for (int item = blockIdx.x; item < a.n_items && ok; item += gridDim.x) {
-        const int q0 = (item / a.S) * TC_M;
+        const int q0 = (item / a.S) * (TC_M * TC_QB);
         const int64_t b_begin = (int64_t)(item % a.S) * a.per;
         const int64_t b_end = b_begin + a.per < a.nb ? b_begin + a.per : a.nb;
         if (a.qres) {
@@ -339,8 +343,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           ok = mbar_wait(qempty0, (iq & 1u) ^ 1u, a.err);
           if (!ok) break;
           mbar_expect_tx(qfull0, (uint32_t)a.qbytes);
-          for (int kc = 0; kc < a.kchunks; ++kc)
-            tma_load_2d(smem_u32(qblock + kc * A_BYTES), &tmQ, kc * TC_K, q0, qfull0);
+          for (int qb = 0; qb < TC_QB; ++qb)
+            for (int kc = 0; kc < a.kchunks; ++kc)
+              tma_load_2d(smem_u32(qblock + (qb * a.kchunks + kc) * A_BYTES), &tmQ, kc * TC_K, q0 + qb * TC_M, qfull0);
           ++iq;
         }
         for (int64_t b0 = b_begin; b0 < b_end && ok; b0 += TC_N) {
@@ -353,8 +358,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             if (a.qres) {
               tma_load_2d(sa, &tmX, kc * TC_K, (int)b0, full0 + 8 * s);
             } else {
-              tma_load_2d(sa, &tmQ, kc * TC_K, q0, full0 + 8 * s);
-              tma_load_2d(sa + A_BYTES, &tmX, kc * TC_K, (int)b0, full0 + 8 * s);
+              for (int qb = 0; qb < TC_QB; ++qb)
+                tma_load_2d(sa + qb * A_BYTES, &tmQ, kc * TC_K, q0 + qb * TC_M, full0 + 8 * s);
+              tma_load_2d(sa + TC_QB * A_BYTES, &tmX, kc * TC_K, (int)b0, full0 + 8 * s);
             }
           }
         }
@@ -378,18 +384,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           ok = mbar_wait(tempty0 + 8 * buf, (use & 1u) ^ 1u, a.err);
           if (!ok) break;
           tc_fence_after();
-          const uint32_t dt = tmem + buf * TC_N;
+          const uint32_t dt = tmem + buf * (TC_QB * TC_N);
           for (int kc = 0; kc < a.kchunks; ++kc, ++it) {
             const uint32_t s = it % NS, ph = (it / NS) & 1u;
             ok = mbar_wait(full0 + 8 * s, ph, a.err);
             if (!ok) break;
             tc_fence_after();
             const uint32_t sa = smem_u32(stage_base + s * a.stage_bytes);
-            const uint32_t qa = a.qres ? smem_u32(qblock + kc * A_BYTES) : sa;
-            const uint32_t xa = a.qres ? sa : sa + A_BYTES;
+            const uint32_t xa = a.qres ? sa : sa + TC_QB * A_BYTES;
 #pragma unroll
-            for (int kk = 0; kk < TC_K / 16; ++kk)
-              tc_mma(dt, smem_desc(qa + kk * 32), smem_desc(xa + kk * 32), a.idesc, (kc | kk) != 0);
+            for (int qb = 0; qb < TC_QB; ++qb) {
+              const uint32_t qa = a.qres ? smem_u32(qblock + (qb * a.kchunks + kc) * A_BYTES) : sa + qb * A_BYTES;
+#pragma unroll
+              for (int kk = 0; kk < TC_K / 16; ++kk)
+                tc_mma(dt + qb * TC_N, smem_desc(qa + kk * 32), smem_desc(xa + kk * 32), a.idesc, (kc | kk) != 0);
+            }
             tc_commit(empty0 + 8 * s);
           }
           if (!ok) break;
@@ -405,14 +414,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // ---------------- epilogue warpgroups ----------------
     const int quarter = warp & 3;            // TMEM lanes 32*quarter .. +31
     const int row = quarter * 32 + lane;
-    const int grp = (warp - 2) >> 2;         // column half of each tile
+    const int grp = (warp - 2) >> 2;         // query block of the item
     float* xw = xn_s + (warp - 2) * 128;     // this warp's copy of its columns' norms
     float* ld = list_d + ((size_t)grp * TC_M + row) * a.k;
     int* li = list_i + ((size_t)grp * TC_M + row) * a.k;
     uint32_t t = 0;
     bool ok = true;
     for (int item = blockIdx.x; item < a.n_items && ok; item += gridDim.x) {
-      const int q = (item / a.S) * TC_M + row;
+      const int q = (item / a.S) * (TC_M * TC_QB) + grp * TC_M + row;
       const int split = item % a.S;
       const int64_t b_begin = (int64_t)split * a.per;
       const int64_t b_end = b_begin + a.per < a.nb ? b_begin + a.per : a.nb;
@@ -427,7 +436,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       unsigned* thr_q = a.thr + (q < a.nq ? q : 0);
       for (int64_t b0 = b_begin; b0 < b_end; b0 += TC_N, ++t) {
         const uint32_t buf = t & 1u, use = t >> 1;
-        const int64_t c_base = b0 + grp * 128;
+        const int64_t c_base = b0;
         const unsigned thr_code = q < a.nq ? __ldcg(a.thr + q) : 0xff800000u;  // other lists' progress (+inf)
         if (a.metric == KANN_L2)
           for (int j = lane; j < 128; j += 32) xw[j] = (c_base + j < b_end) ? __ldg(a.xnorm + c_base + j) : 0.f;
@@ -438,7 +447,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll 1
         for (int c0 = 0; c0 < 128; c0 += 64) {
           float v[64];
-          tc_ld64(tmem + ((uint32_t)(quarter * 32) << 16) + buf * TC_N + grp * 128 + c0, v);
+          tc_ld64(tmem + ((uint32_t)(quarter * 32) << 16) + buf * (TC_QB * TC_N) + grp * TC_N + c0, v);
           const int64_t cb = c_base + c0;
           // pass 1: scores and the minimum of each group of 16 columns
           float mn[4];
@@ -486,7 +495,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       if (!ok) break;
       if (q < a.nq) {
         const float qn = a.metric == KANN_L2 ? a.qnorm[q] : 0.f;
-        u64* o = a.out + (((size_t)q * a.S + split) * 2 + grp) * a.k;
+        u64* o = a.out + ((size_t)q * a.S + split) * a.k;
         for (int j = 0; j < a.k; ++j)
           o[j] = li[j] < 0 ? ((u64)ordered_bits(__int_as_float(0x7f800000)) << 32) | 0xffffffffull
                            : make_key(ld[j] + qn, (uint32_t)li[j]);
@@ -648,10 +657,11 @@ int num_sms() {
 
 }  // namespace
 
-// Work split of the tensor-core path: queries in tiles of 128, the base in S
-// splits (multiples of 256 rows) so that there are >= 4 work items per SM.
+// Work split of the tensor-core path: queries in pairs of 128-row tiles, the
+// base in S splits (multiples of 128 rows) so that there are >= 4 work items
+// per SM.
 void exact_tc_plan(int nq, int64_t nb, int* S_out, int64_t* per_out) {
-  const int qtiles = (nq + TC_M - 1) / TC_M;
+  const int qtiles = (nq + TC_M * TC_QB - 1) / (TC_M * TC_QB);
   const int64_t ntiles = (nb + TC_N - 1) / TC_N;
   int S = (4 * 148 + qtiles - 1) / qtiles;
   if (S > 64) S = 64;
@@ -667,7 +677,7 @@ size_t exact_tc_workspace_bytes(int nq, int64_t nb, int k) {
   int S;
   int64_t per;
   exact_tc_plan(nq, nb, &S, &per);
-  return (size_t)nq * S * 2 * k * 8 + (size_t)nb * 4 + (size_t)nq * 8 + 256;
+  return (size_t)nq * S * k * 8 + (size_t)nb * 4 + (size_t)nq * 8 + 256;
 }
 
 bool exact_tc_supported(int dtype, int d, int k) {
@@ -681,7 +691,7 @@ int exact_tc_run(const void* Q, const void* X, int nq, int64_t nb, int d, int me
   exact_tc_plan(nq, nb, &S, &per);
   unsigned char* w = static_cast<unsigned char*>(ws);
   u64* part = reinterpret_cast<u64*>(w);
-  float* xn = reinterpret_cast<float*>(w + (size_t)nq * S * 2 * k * 8);
+  float* xn = reinterpret_cast<float*>(w + (size_t)nq * S * k * 8);
   float* qn = xn + nb;
   unsigned* th = reinterpret_cast<unsigned*>(qn + nq);
   int* err = reinterpret_cast<int*>(((uintptr_t)(th + nq) + 15) & ~(uintptr_t)15);
@@ -706,7 +716,7 @@ int exact_tc_run(const void* Q, const void* X, int nq, int64_t nb, int d, int me
   a.S = S;
   a.kchunks = (d + TC_K - 1) / TC_K;
   a.per = per;
-  a.n_items = ((nq + TC_M - 1) / TC_M) * S;
+  a.n_items = ((nq + TC_M * TC_QB - 1) / (TC_M * TC_QB)) * S;
   a.idesc = make_idesc(dtype);
   a.xnorm = xn;
   a.qnorm = qn;
@@ -720,8 +730,8 @@ int exact_tc_run(const void* Q, const void* X, int nq, int64_t nb, int d, int me
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   // resident query block when it and a ring of at least 3 base stages fit
   a.qres = a.kchunks <= TC_QRES_MAX_KCHUNKS &&
-           fixed + (size_t)a.kchunks * A_BYTES + 3 * (size_t)B_BYTES <= (size_t)optin;
-  a.qbytes = a.qres ? a.kchunks * A_BYTES : 0;
+           fixed + (size_t)TC_QB * a.kchunks * A_BYTES + 3 * (size_t)B_BYTES <= (size_t)optin;
+  a.qbytes = a.qres ? TC_QB * a.kchunks * A_BYTES : 0;
   a.stage_bytes = a.qres ? B_BYTES : STAGE_BYTES;
   a.stages = TC_MAX_STAGES;
   while (a.stages > 2 && fixed + (size_t)a.qbytes + (size_t)a.stages * a.stage_bytes > (size_t)optin) --a.stages;
@@ -733,13 +743,13 @@ int exact_tc_run(const void* Q, const void* X, int nq, int64_t nb, int d, int me
   e = cudaGetLastError();
   if (e != cudaSuccess) return (int)e;
   int P = 32;
-  while (P < 2 * S * k) P <<= 1;
+  while (P < S * k) P <<= 1;
   int wpb = 4;
   while (wpb > 1 && (size_t)wpb * P * 8 > 160 * 1024) wpb >>= 1;
   const size_t msmem = (size_t)wpb * P * 8;
   e = cudaFuncSetAttribute(exact_tc_merge_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msmem);
   if (e != cudaSuccess) return (int)e;
-  exact_tc_merge_kernel<<<(nq + wpb - 1) / wpb, wpb * 32, msmem, s>>>(part, err, nq, 2 * S, k, P, ids, dists);
+  exact_tc_merge_kernel<<<(nq + wpb - 1) / wpb, wpb * 32, msmem, s>>>(part, err, nq, S, k, P, ids, dists);
   return (int)cudaGetLastError();
 }
 

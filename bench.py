@@ -1063,7 +1063,7 @@ def main():
                        "launch_settings": {"fp16_rerank": tuned16, "fp32": tuned32, "tune_s": tune_s,
                                            "rule": "autotuner: fastest of the result-preserving settings "
                                                    "(visited table layout and size, lanes per row, warps "
-                                                   "per CTA, lean, persistent), same ids and distances "
+                                                   "per CTA, team size, lean, persistent), same ids and distances "
                                                    "as the default launch"},
                        "host_cores": os.cpu_count()},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,

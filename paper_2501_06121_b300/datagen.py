@@ -174,7 +174,13 @@ def _sparse_rows(rng, m, vocab, lam, cdf, wsigma):
             todo = np.array(still, dtype=np.int64)
         for r in range(e - s):
             terms[indptr[s + r]:indptr[s + r + 1]] = rows[r]
-    weights = np.exp(wsigma * rng.standard_normal(indptr[-1])).astype(np.float32)
+    # weights in blocks of 2^22 draws (the same stream as one draw of all of
+    # them, with bounded temporaries at 8.8M documents)
+    weights = np.empty(indptr[-1], np.float32)
+    wstep = 1 << 22
+    for s in range(0, len(weights), wstep):
+        e = min(len(weights), s + wstep)
+        weights[s:e] = np.exp(wsigma * rng.standard_normal(e - s))
     return indptr, terms, weights
 
 

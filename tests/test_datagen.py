@@ -52,3 +52,14 @@ def test_vmf_blocks_are_the_rows_of_the_whole_draw():
         blocks, Qb = G.vmf_mixture_blocks(70000, 50, d=16, clusters=8, seed=9, concentration=conc)
         Xb = np.concatenate([b for _, b in blocks])
         assert np.array_equal(X, Xb) and np.array_equal(Q, Qb)
+
+
+def test_sparse_weights_in_blocks_are_the_stream_of_one_draw():
+    # the sparse generator draws its weights in blocks of 2^22; the blocks are
+    # the values one draw of all of them gives (same generator state)
+    rng = np.random.default_rng(12)
+    n = (1 << 22) + 12345
+    one = np.exp(0.5 * rng.standard_normal(n)).astype(np.float32)
+    rng = np.random.default_rng(12)
+    blocks = np.concatenate([np.exp(0.5 * rng.standard_normal(m)) for m in (1 << 22, 12345)]).astype(np.float32)
+    assert np.array_equal(one, blocks)

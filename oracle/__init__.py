@@ -34,49 +34,54 @@ _u64 = ctypes.c_uint64
 def lib():
     global _lib
     if _lib is None:
-        path = _build.build()
-        L = ctypes.CDLL(path)
-        sig = {
-            "orc_encode_f16": [_p, _i64, _p],
-            "orc_encode_bf16": [_p, _i64, _p],
-            "orc_decode_f16": [_p, _i64, _p],
-            "orc_decode_bf16": [_p, _i64, _p],
-            "orc_decode_e4m3": [_p, _i64, _p],
-            "orc_encode_e4m3_rows": [_p, _i64, _i32, _p, _p],
-            "orc_splitmix64_seq": [_u64, _i64, _p],
-            "orc_levels": [_i64, _i32, _u64, _p],
-            "orc_graph_build_dense": [_i32, _p, _p, _i64, _i32, _i32, _i32, _i32, _u64, _i32],
-            "orc_graph_build_sparse": [_p, _p, _p, _i64, _i32, _i32, _u64, _i32],
-            "orc_graph_free": [_p],
-            "orc_graph_info": [_p, _p],
-            "orc_graph_export": [_p, _p, _p, _p, _p],
-            "orc_graph_import": [_i64, _i32, _i32, _i32, _i64, _p, _p, _p, _p],
-            "orc_search_dense": [_p, _i32, _p, _p, _i32, _i32, _p, _i64, _i32, _i32, _i32, _i64, _i32,
-                                 _p, _p, _p],
-            "orc_search_dense_multi": [_p, _i32, _p, _p, _i32, _i32, _p, _i64, _i32, _i32, _i32, _i32, _p, _p, _p],
-            "orc_search_pq": [_p, _p, _p, _i32, _i32, _i32, _i32, _i32, _p, _i64, _i32, _i32, _i32, _i32, _p, _p,
-                              _p],
-            "orc_search_sparse": [_p, _p, _p, _p, _p, _p, _p, _i64, _i32, _i32, _i32, _i32, _p, _p, _p],
-            "orc_rerank_dense": [_i32, _p, _p, _i32, _i32, _p, _i64, _p, _i32, _i32, _p, _p],
-            "orc_dist_dense": [_i32, _p, _p, _i32, _i32, _p, _i64, _p, _i32, _p],
-            "orc_exact_dense": [_i32, _p, _p, _i64, _i32, _i32, _p, _i64, _i32, _i32, _p, _p],
-            "orc_exact_sparse": [_p, _p, _p, _i64, _p, _p, _p, _i64, _i32, _i32, _p, _p],
-            "orc_exact_pq": [_p, _p, _i64, _i32, _i32, _i32, _i32, _p, _i64, _i32, _p, _p],
-            "orc_pq_lut": [_p, _i32, _i32, _i32, _i32, _i32, _p, _p],
-            "orc_pq_lut_u8": [_p, _i32, _i32, _i32, _i32, _p, _p, _p, _p],
-            "orc_pq_encode": [_p, _i64, _i32, _i32, _i32, _p, _p],
-            "orc_pq_reconstruct": [_p, _i64, _i32, _i32, _i32, _p, _p],
-            "orc_pq_train": [_p, _i64, _i32, _i32, _i32, _i32, _u64, _p, _p],
-        }
-        for name, args in sig.items():
-            f = getattr(L, name)
-            f.argtypes = args
-            f.restype = None
-        L.orc_graph_build_dense.restype = _p
-        L.orc_graph_build_sparse.restype = _p
-        L.orc_graph_import.restype = _p
-        _lib = L
+        _lib = load(_build.build())
     return _lib
+
+
+def load(path):
+    """The oracle library at `path` with its argument types set (lib() loads
+    the built oracle; the tests also load copies with planted mistakes)."""
+    L = ctypes.CDLL(path)
+    sig = {
+        "orc_encode_f16": [_p, _i64, _p],
+        "orc_encode_bf16": [_p, _i64, _p],
+        "orc_decode_f16": [_p, _i64, _p],
+        "orc_decode_bf16": [_p, _i64, _p],
+        "orc_decode_e4m3": [_p, _i64, _p],
+        "orc_encode_e4m3_rows": [_p, _i64, _i32, _p, _p],
+        "orc_splitmix64_seq": [_u64, _i64, _p],
+        "orc_levels": [_i64, _i32, _u64, _p],
+        "orc_graph_build_dense": [_i32, _p, _p, _i64, _i32, _i32, _i32, _i32, _u64, _i32],
+        "orc_graph_build_sparse": [_p, _p, _p, _i64, _i32, _i32, _u64, _i32],
+        "orc_graph_free": [_p],
+        "orc_graph_info": [_p, _p],
+        "orc_graph_export": [_p, _p, _p, _p, _p],
+        "orc_graph_import": [_i64, _i32, _i32, _i32, _i64, _p, _p, _p, _p],
+        "orc_search_dense": [_p, _i32, _p, _p, _i32, _i32, _p, _i64, _i32, _i32, _i32, _i64, _i32,
+                             _p, _p, _p],
+        "orc_search_dense_multi": [_p, _i32, _p, _p, _i32, _i32, _p, _i64, _i32, _i32, _i32, _i32, _p, _p, _p],
+        "orc_search_pq": [_p, _p, _p, _i32, _i32, _i32, _i32, _i32, _p, _i64, _i32, _i32, _i32, _i32, _p, _p,
+                          _p],
+        "orc_search_sparse": [_p, _p, _p, _p, _p, _p, _p, _i64, _i32, _i32, _i32, _i32, _p, _p, _p],
+        "orc_rerank_dense": [_i32, _p, _p, _i32, _i32, _p, _i64, _p, _i32, _i32, _p, _p],
+        "orc_dist_dense": [_i32, _p, _p, _i32, _i32, _p, _i64, _p, _i32, _p],
+        "orc_exact_dense": [_i32, _p, _p, _i64, _i32, _i32, _p, _i64, _i32, _i32, _p, _p],
+        "orc_exact_sparse": [_p, _p, _p, _i64, _p, _p, _p, _i64, _i32, _i32, _p, _p],
+        "orc_exact_pq": [_p, _p, _i64, _i32, _i32, _i32, _i32, _p, _i64, _i32, _p, _p],
+        "orc_pq_lut": [_p, _i32, _i32, _i32, _i32, _i32, _p, _p],
+        "orc_pq_lut_u8": [_p, _i32, _i32, _i32, _i32, _p, _p, _p, _p],
+        "orc_pq_encode": [_p, _i64, _i32, _i32, _i32, _p, _p],
+        "orc_pq_reconstruct": [_p, _i64, _i32, _i32, _i32, _p, _p],
+        "orc_pq_train": [_p, _i64, _i32, _i32, _i32, _i32, _u64, _p, _p],
+    }
+    for name, args in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = None
+    L.orc_graph_build_dense.restype = _p
+    L.orc_graph_build_sparse.restype = _p
+    L.orc_graph_import.restype = _p
+    return L
 
 
 def _ptr(a):

@@ -12,13 +12,20 @@ SRC = os.path.join(HERE, "kann_oracle.cpp")
 LIB = os.path.join(HERE, "liboracle.so")
 
 
+def compile_source(src: str, out: str) -> str:
+    """Compile an oracle source file into the shared library `out` (the
+    oracle's own flags; the tests also build copies with planted mistakes)."""
+    cmd = ["g++", "-std=c++17", "-O2", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
+           "-shared", "-fPIC", "-o", out, src]
+    subprocess.check_call(cmd)
+    return out
+
+
 def build(force: bool = False) -> str:
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= os.path.getmtime(SRC):
         return LIB
     tmp = LIB + ".tmp%d" % os.getpid()
-    cmd = ["g++", "-std=c++17", "-O2", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
-           "-shared", "-fPIC", "-o", tmp, SRC]
-    subprocess.check_call(cmd)
+    compile_source(SRC, tmp)
     os.replace(tmp, LIB)
     return LIB
 

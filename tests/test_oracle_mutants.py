@@ -1,0 +1,93 @@
+"""Planted mistakes in the oracle, on the CPU: each case is the oracle's source
+with one plausible mistake -- a dropped term, a wrong sign, a wrong index, a
+reversed or lost tie-break, a wrong constant in the level law, the wrong
+candidate expanded first -- built into a library of its own.  The named pins
+(the oracle's own tests, which check it against closed forms, numpy and
+hand-worked goldens) must fail on every such copy; on the real oracle they
+pass (they run in the suite).  This is the evidence that the pins would catch
+the mistake, not only that the oracle agrees with itself."""
+import gc
+import os
+from concurrent.futures import ThreadPoolExecutor
+
+import pytest
+
+import oracle as O
+import test_oracle_levels as TL
+import test_oracle_pq as TP
+import test_oracle_rerank as TR
+import test_oracle_search as TS
+import test_oracle_sparse as TSp
+from oracle import build as OB
+
+# name: (text in kann_oracle.cpp, its replacement, pins that must fail)
+MUTANTS = {
+    "l2_drops_the_last_dimension": (
+        "for (int k = 0; k < d; ++k) { double t = q[k] - x(j, k); s += t * t; }",
+        "for (int k = 0; k + 1 < d; ++k) { double t = q[k] - x(j, k); s += t * t; }",
+        [lambda: TS.test_brute_force_when_ef_covers_n(O.L2)]),
+    "ip_with_the_wrong_sign": (
+        "for (int k = 0; k < d; ++k) s -= q[k] * x(j, k);",
+        "for (int k = 0; k < d; ++k) s += q[k] * x(j, k);",
+        [lambda: TS.test_brute_force_when_ef_covers_n(O.IP)]),
+    "pq_table_reads_the_wrong_query_subvector": (
+        "double qq = qv[j * dsub + t], cc = C[t];",
+        "double qq = qv[t], cc = C[t];",
+        [TP.test_adc_equals_exact_distance_to_reconstruction]),
+    "sparse_ip_drops_the_query_weight": (
+        "s += (double)wa[i] * wb;",
+        "s += (double)wa[i];",
+        [TSp.test_sparse_ip_equals_densified_ip]),
+    "ties_go_to_the_higher_id": (
+        "return a.id < b.id;",
+        "return a.id > b.id;",
+        [TS.test_duplicates_ordered_by_id_and_self_query,
+         lambda: TR.test_rerank_equals_numpy_lexsort_on_tied_integer_rows(O.L2, False)]),
+    "rerank_keeps_candidate_order_on_ties": (
+        "std::sort(cs.begin(), cs.end(), CandLess());",
+        "std::stable_sort(cs.begin(), cs.end(), [](const Cand& a, const Cand& b) { return a.d < b.d; });",
+        [lambda: TR.test_rerank_equals_numpy_lexsort_on_tied_integer_rows(O.L2, True)]),
+    "level_law_with_base_m_plus_one": (
+        "std::log((double)M)",
+        "std::log((double)M + 1.0)",
+        [lambda: TL.test_level_law_chi_square(16)]),
+    "search_expands_the_worst_unexpanded_entry": (
+        "size_t c = 0;\n    while (c < W.size() && expanded[c]) ++c;",
+        "size_t c = W.size();\n    for (size_t t = W.size(); t-- > 0;) if (!expanded[t]) { c = t; break; }",
+        [lambda: TS.test_hand_worked_golden(O.FORM_FLAGS)]),
+}
+
+
+@pytest.fixture(scope="module")
+def mutant_libs(tmp_path_factory):
+    d = tmp_path_factory.mktemp("oracle_mutants")
+    with open(OB.SRC) as f:
+        src = f.read()
+
+    def one(name):
+        old, new, _ = MUTANTS[name]
+        assert src.count(old) == 1, name  # the planted change hits exactly one place
+        path = os.path.join(str(d), name + ".cpp")
+        with open(path, "w") as f:
+            f.write(src.replace(old, new))
+        return name, OB.compile_source(path, os.path.join(str(d), name + ".so"))
+
+    with ThreadPoolExecutor(max_workers=len(MUTANTS)) as ex:
+        return dict(ex.map(one, MUTANTS))
+
+
+@pytest.mark.parametrize("name", list(MUTANTS))
+def test_pins_catch_the_planted_mistake(mutant_libs, name):
+    real = O.lib()
+    O._lib = O.load(mutant_libs[name])
+    try:
+        caught = 0
+        for pin in MUTANTS[name][2]:
+            try:
+                pin()
+            except AssertionError:
+                caught += 1
+        assert caught == len(MUTANTS[name][2]), "a pin passed on the mutant %s" % name
+    finally:
+        gc.collect()  # graphs built by the mutant are freed while it is loaded
+        O._lib = real

@@ -1,9 +1,10 @@
 """Planted mistakes in the oracle, on the CPU: each case is the oracle's source
 with one plausible mistake -- a dropped term, a wrong sign, a wrong index, a
-reversed or lost tie-break, a wrong constant in the level law, the wrong
-candidate expanded first -- built into a library of its own.  The named pins
-(the oracle's own tests, which check it against closed forms, numpy and
-hand-worked goldens) must fail on every such copy; on the real oracle they
+reversed or lost tie-break, a wrong rounding or constant, a wrong step of the
+descent, the wrong candidate expanded first -- built into a library of its
+own.  The named pins
+(the oracle's own tests, which check it against closed forms, numpy, torch's
+casts and hand-worked goldens) must fail on every such copy; on the real oracle they
 pass (they run in the suite).  This is the evidence that the pins would catch
 the mistake, not only that the oracle agrees with itself."""
 import gc
@@ -13,6 +14,7 @@ from concurrent.futures import ThreadPoolExecutor
 import pytest
 
 import oracle as O
+import test_oracle_formats as TF
 import test_oracle_levels as TL
 import test_oracle_pq as TP
 import test_oracle_rerank as TR
@@ -51,6 +53,26 @@ MUTANTS = {
         "std::log((double)M)",
         "std::log((double)M + 1.0)",
         [lambda: TL.test_level_law_chi_square(16)]),
+    "fp16_rounds_ties_away_from_zero": (
+        "double r = std::nearbyint(a / quantum);",
+        "double r = std::round(a / quantum);",
+        [TF.test_f16_encode_matches_numpy_rne]),
+    "e4m3_scale_divides_by_447": (
+        "float s = mx / 448.0f;",
+        "float s = mx / 447.0f;",
+        [TF.test_e4m3_rows_match_torch_cast_and_error_bound]),
+    "u8_table_forgets_the_subspace_minimum": (
+        "const float r = std::fmin(std::fmax((e[(size_t)j * ksub + c] - mn[j]) / t.scale, 0.f), 255.f);",
+        "const float r = std::fmin(std::fmax((e[(size_t)j * ksub + c]) / t.scale, 0.f), 255.f);",
+        [lambda: TP.test_u8_table_equals_its_definition_written_in_numpy(O.L2)]),
+    "pq_encode_ties_to_the_highest_centroid": (
+        "if (s < best) { best = s; bc = c; }\n      }\n      codes[(size_t)i * m + j] = (uint8_t)bc;",
+        "if (s <= best) { best = s; bc = c; }\n      }\n      codes[(size_t)i * m + j] = (uint8_t)bc;",
+        [TP.test_encode_picks_nearest_and_lowest_on_ties]),
+    "greedy_descent_takes_the_first_better_neighbour": (
+        "if (cand_less(ce, best)) best = ce;",
+        "if (cand_less(ce, cur)) { best = ce; break; }",
+        [lambda: TS.test_hand_worked_golden(O.FORM_FLAGS)]),
     "search_expands_the_worst_unexpanded_entry": (
         "size_t c = 0;\n    while (c < W.size() && expanded[c]) ++c;",
         "size_t c = W.size();\n    for (size_t t = W.size(); t-- > 0;) if (!expanded[t]) { c = t; break; }",

@@ -17,7 +17,7 @@ import pytest
 import torch
 
 import oracle as O
-from helpers import id_set_match_fraction, recall
+from helpers import golden_graph, id_set_match_fraction, load_golden, recall
 from paper_2501_06121_b300 import kann as K
 
 pytestmark = pytest.mark.gpu
@@ -117,3 +117,21 @@ def test_multi_expansion_option_checks(cfg1_small):
                                                                     metric=K.KANN_L2))
     with pytest.raises(K.KannError):
         search(ip, Q[:4], 10, 32, expand=2)
+
+
+def test_multi_expansion_hand_worked_golden_on_gpu():
+    # the hand-worked multi-expansion cases (ids, distances and work counters)
+    gold = {c["name"]: c for c in load_golden("hand_search.json")["cases"]}
+    multi = load_golden("hand_search_multi.json")
+    for mc in multi["cases"]:
+        case = gold[mc["name"]]
+        X = np.zeros((len(case["x"]), 4), np.float32)
+        X[:, 0] = case["x"]  # padded to 16 bytes per row; L2 unchanged
+        q = np.zeros((1, 4), np.float32)
+        q[0, 0] = case["q"]
+        idx = K.kann_index_upload(K.graph_to_device(golden_graph(case)), vectors=dev(X))
+        for run in mc["runs"]:
+            cnt = torch.zeros((1, 4), dtype=torch.int32, device="cuda")
+            gi, gd = search(idx, q, run["k"], run["ef"], expand=multi["p"], counters=cnt)
+            assert gi[0].tolist() == run["ids"] and gd[0].tolist() == run["dists"], (mc["name"], run)
+            assert cnt.cpu().numpy()[0].tolist() == run["counters"], (mc["name"], run)

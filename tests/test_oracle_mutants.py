@@ -73,6 +73,32 @@ MUTANTS = {
         "if (cand_less(ce, best)) best = ce;",
         "if (cand_less(ce, cur)) { best = ce; break; }",
         [lambda: TS.test_hand_worked_golden(O.FORM_FLAGS)]),
+    "bf16_keeps_one_bit_less": (
+        "double v = round_to_format((double)x, 8, -126, std::ldexp(255.0, 120), false);",
+        "double v = round_to_format((double)x, 7, -126, std::ldexp(255.0, 120), false);",
+        [TF.test_bf16_encode_matches_torch]),
+    "e4m3_decode_exponent_bias_off_by_one": (
+        "else v = std::ldexp(8.0 + m, e - 10);",
+        "else v = std::ldexp(8.0 + m, e - 11);",
+        [TF.test_e4m3_decode_all_codes]),
+    "fp16_subnormals_start_one_binade_low": (
+        "double v = round_to_format((double)x, 11, -14, 65504.0, false);",
+        "double v = round_to_format((double)x, 11, -15, 65504.0, false);",
+        [TF.test_f16_encode_matches_numpy_rne]),
+    "rerank_scores_inner_product_as_l2": (
+        "DenseSpace sp(dtype, data, scale, d, metric);\n  for (int64_t qi = 0; qi < nq; ++qi) {\n"
+        "    sp.set_query(queries + (size_t)qi * d);\n    std::vector<Cand> cs;",
+        "DenseSpace sp(dtype, data, scale, d, MET_L2);\n  for (int64_t qi = 0; qi < nq; ++qi) {\n"
+        "    sp.set_query(queries + (size_t)qi * d);\n    std::vector<Cand> cs;",
+        [lambda: TR.test_rerank_equals_numpy_lexsort_on_tied_integer_rows(O.IP, False)]),
+    "two_heap_search_stops_at_the_first_equal": (
+        "if (cand_less(f, c)) break;  // c is further than the furthest kept",
+        "if (!cand_less(c, f)) break;",
+        [lambda: TS.test_hand_worked_golden(O.FORM_TWO_HEAP)]),
+    "multi_expansion_takes_one_entry_too_many": (
+        "for (size_t c = 0; c < W.size() && (int)chosen.size() < p; ++c) {",
+        "for (size_t c = 0; c < W.size() && (int)chosen.size() <= p; ++c) {",
+        [TS.test_multi_expansion_hand_worked_golden]),
     "search_expands_the_worst_unexpanded_entry": (
         "size_t c = 0;\n    while (c < W.size() && expanded[c]) ++c;",
         "size_t c = W.size();\n    for (size_t t = W.size(); t-- > 0;) if (!expanded[t]) { c = t; break; }",

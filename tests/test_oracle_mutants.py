@@ -99,6 +99,18 @@ MUTANTS = {
         "for (size_t c = 0; c < W.size() && (int)chosen.size() < p; ++c) {",
         "for (size_t c = 0; c < W.size() && (int)chosen.size() <= p; ++c) {",
         [TS.test_multi_expansion_hand_worked_golden]),
+    "search_lets_a_forgotten_id_into_w_twice": (
+        "if (pos < W.size() && W[pos].id == ce.id) continue;  // already in W",
+        "",
+        [lambda: TS.test_forgetful_visited_set_changes_nothing_on_tied_integer_data(1)]),
+    "adc_sum_skips_the_last_subspace": (
+        "for (int j = 0; j < m; ++j) s += lut[(size_t)j * ksub + ci[j]];",
+        "for (int j = 0; j + 1 < m; ++j) s += lut[(size_t)j * ksub + ci[j]];",
+        [TP.test_pq_is_exact_when_every_subvector_is_a_centroid]),
+    "u8_distance_offset_skips_a_minimum": (
+        "for (int j = 0; j < m; ++j) sm += mn[j];",
+        "for (int j = 0; j + 1 < m; ++j) sm += mn[j];",
+        [lambda: TP.test_u8_table_equals_its_definition_written_in_numpy(O.L2)]),
     "search_expands_the_worst_unexpanded_entry": (
         "size_t c = 0;\n    while (c < W.size() && expanded[c]) ++c;",
         "size_t c = W.size();\n    for (size_t t = W.size(); t-- > 0;) if (!expanded[t]) { c = t; break; }",

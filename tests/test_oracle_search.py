@@ -67,6 +67,22 @@ def test_forgetful_visited_set_changes_nothing(cfg1_small, cap):
     assert np.all(b[2][:, 0] >= a[2][:, 0])  # forgetting only adds work
 
 
+@pytest.mark.parametrize("cap", [1, 3])
+def test_forgetful_visited_set_changes_nothing_on_tied_integer_data(cap):
+    # a table that forgets almost everything re-evaluates ids over and over;
+    # the search must still return W's ids once each (equal (d, id) keys are
+    # caught before they enter W twice), on data with many exact ties
+    rng = np.random.default_rng(31)
+    X = rng.integers(0, 6, (600, 6)).astype(np.float32)
+    Q = rng.integers(0, 6, (60, 6)).astype(np.float32)
+    g = O.build_dense(X, O.L2, 6, 40, 31)
+    a = O.search_dense(g, X, Q, 10, 48, O.L2, visited_cap=0)
+    b = O.search_dense(g, X, Q, 10, 48, O.L2, visited_cap=cap)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    assert all(len(set(r)) == len(r) for r in b[0])
+    assert np.all(b[2][:, 0] >= a[2][:, 0])
+
+
 def test_recall_reaches_one_and_grows_with_ef(cfg1_small):
     X, Q, g = cfg1_small
     ei, _ = O.exact_dense(X, Q[:100], 10, O.L2)

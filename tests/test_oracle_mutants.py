@@ -111,6 +111,14 @@ MUTANTS = {
         "for (int j = 0; j < m; ++j) sm += mn[j];",
         "for (int j = 0; j + 1 < m; ++j) sm += mn[j];",
         [lambda: TP.test_u8_table_equals_its_definition_written_in_numpy(O.L2)]),
+    "lloyd_mean_divides_by_count_plus_one": (
+        "C[(size_t)c * dsub + t] = sum[(size_t)c * dsub + t] / (double)cnt[c];",
+        "C[(size_t)c * dsub + t] = sum[(size_t)c * dsub + t] / (double)(cnt[c] + 1);",
+        [TP.test_pq_is_exact_when_every_subvector_is_a_centroid]),
+    "e4m3_rows_ignore_their_scale": (
+        "default: return decode_e4m3(((const uint8_t*)data)[o]) * (double)scale[j];",
+        "default: return decode_e4m3(((const uint8_t*)data)[o]);",
+        [TR.test_distances_on_stored_fp16_and_e4m3_rows_decode_them]),
     "search_expands_the_worst_unexpanded_entry": (
         "size_t c = 0;\n    while (c < W.size() && expanded[c]) ++c;",
         "size_t c = W.size();\n    for (size_t t = W.size(); t-- > 0;) if (!expanded[t]) { c = t; break; }",

@@ -78,3 +78,23 @@ def test_rerank_of_stored_formats_decodes_them():
     ni, nd = numpy_rerank(Xdec, Q, cand, 10, O.L2)
     assert np.array_equal(oi, ni)
     assert np.allclose(od, nd, rtol=1e-12, atol=0)
+
+
+def test_distances_on_stored_fp16_and_e4m3_rows_decode_them():
+    # the oracle's distances on FP16 and per-vector-scaled E4M3 rows against
+    # numpy on rows decoded by the formats' definitions (numpy's float16,
+    # torch's float8_e4m3fn, times the row's scale)
+    import torch
+    rng = np.random.default_rng(14)
+    X = (rng.standard_normal((300, 32)) * 3).astype(np.float32)
+    Q = rng.standard_normal((10, 32)).astype(np.float32)
+    ids = np.tile(np.arange(300, dtype=np.int32), (len(Q), 1))
+    h = X.astype(np.float16)
+    got = O.dist_dense(h.view(np.uint16), Q, ids, O.L2, dtype=O.DT_F16)
+    ref = ((Q.astype(np.float64)[:, None] - h.astype(np.float64)[None]) ** 2).sum(-1)
+    assert np.allclose(got, ref, rtol=1e-12, atol=0)
+    codes, sc = O.encode_e4m3_rows(X)
+    dec = torch.from_numpy(codes).view(torch.float8_e4m3fn).double().numpy() * sc.astype(np.float64)[:, None]
+    got = O.dist_dense(codes, Q, ids, O.IP, dtype=O.DT_E4M3, scale=sc)
+    ref = -(Q.astype(np.float64) @ dec.T)
+    assert np.allclose(got, ref, rtol=1e-12, atol=1e-12)

@@ -483,11 +483,16 @@ def run_pq768(args, n=None, concentration=None):
             ms8, (ids8, _) = timed(lambda: K_.kann_search_ex(idx_pq, Qd, k, ef, rerank=100 if k <= 100 else -1,
                                                              pq_lut=K_.KANN_PQ_LUT_U8))
             r8 = recall_at(ids8.cpu().numpy(), gt100, k)
+            # the uint8 table with every beam entry re-ranked (R = ef): the
+            # recall a fixed R of 100 caps at k = 100
+            mse, (idse, _) = timed(lambda: K_.kann_search_ex(idx_pq, Qd, k, ef, rerank=-1, pq_lut=K_.KANN_PQ_LUT_U8))
+            re_ = recall_at(idse.cpu().numpy(), gt100, k)
             ms32, (ids32, _) = timed(lambda: K_.kann_search_ex(idx32, Qd, k, ef))
             r32 = recall_at(ids32.cpu().numpy(), gt100, k)
             rows.append({"k": k, "ef": ef, "pq_rerank100_qps": 1e4 / (ms / 1e3), "pq_rerank100_recall": r,
                          "pq_f16table_rerank100_qps": 1e4 / (ms16 / 1e3), "pq_f16table_rerank100_recall": r16,
                          "pq_u8table_rerank100_qps": 1e4 / (ms8 / 1e3), "pq_u8table_rerank100_recall": r8,
+                         "pq_u8table_rerank_ef_qps": 1e4 / (mse / 1e3), "pq_u8table_rerank_ef_recall": re_,
                          "fp32_qps": 1e4 / (ms32 / 1e3), "fp32_recall": r32})
             print(json.dumps(rows[-1]), flush=True)
     out = {"workload": "pq768", "n": n, "concentration": concentration,

@@ -119,6 +119,14 @@ MUTANTS = {
         "default: return decode_e4m3(((const uint8_t*)data)[o]) * (double)scale[j];",
         "default: return decode_e4m3(((const uint8_t*)data)[o]);",
         [TR.test_distances_on_stored_fp16_and_e4m3_rows_decode_them]),
+    "fp16_table_keeps_one_bit_less": (
+        "for (double& v : lut) v = std::ldexp(round_to_format(std::ldexp(v, -e), 11, -14, 65504.0, false), e);",
+        "for (double& v : lut) v = std::ldexp(round_to_format(std::ldexp(v, -e), 10, -14, 65504.0, false), e);",
+        [TP.test_fp16_table_is_the_scaled_half_rounding_of_the_fp64_table]),
+    "sparse_query_loses_its_last_term": (
+        "qt.assign(t, t + nnz);",
+        "qt.assign(t, t + (nnz > 0 ? nnz - 1 : 0));",
+        [TSp.test_sparse_ip_equals_densified_ip]),
     "search_expands_the_worst_unexpanded_entry": (
         "size_t c = 0;\n    while (c < W.size() && expanded[c]) ++c;",
         "size_t c = W.size();\n    for (size_t t = W.size(); t-- > 0;) if (!expanded[t]) { c = t; break; }",
